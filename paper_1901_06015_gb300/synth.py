@@ -1,0 +1,86 @@
+"""Seeded synthetic inputs for mixed-datatype gemm.
+
+This module only draws random matrices; it holds none of the method's arithmetic.
+Both the oracle-based tests and the CUDA path take their inputs from here.
+
+Recipe (the paper's experiments use randomized, column-stored matrices with
+alpha = beta = 1, Sec. 8.2.1; no dataset is involved):
+  * ``numpy.random.default_rng(seed)``; fill order A.re, A.im, B.re, B.im, C.re, C.im;
+    each component drawn in float64 then rounded (RN-even) to the storage type.
+  * "uniform": each real component ~ U[-1, 1].
+  * "loguniform": sign * 10**U(-4, 4) with a random sign (magnitudes 1e-4..1e4).
+  * "smallint": integers in {-4, ..., 4}; with these, every product and partial sum
+    of a gemm with k <= 1024 is an integer below 2**24, so exact in every precision.
+"""
+import numpy as np
+
+NP_OF_DT = {"s": np.float32, "d": np.float64, "c": np.complex64, "z": np.complex128}
+DTS = ("s", "d", "c", "z")
+
+
+def all_combos():
+    """All 128 labels ``cabx``: C, A, B storage datatypes then computation precision."""
+    return [c + a + b + x for c in DTS for a in DTS for b in DTS for x in ("s", "d")]
+
+
+def is_complex(dt):
+    return dt in ("c", "z")
+
+
+def _component(rng, shape, dist):
+    if dist == "uniform":
+        return rng.uniform(-1.0, 1.0, size=shape)
+    if dist == "loguniform":
+        mag = 10.0 ** rng.uniform(-4.0, 4.0, size=shape)
+        sign = np.where(rng.uniform(size=shape) < 0.5, -1.0, 1.0)
+        return sign * mag
+    if dist == "smallint":
+        return rng.integers(-4, 5, size=shape).astype(np.float64)
+    raise ValueError(dist)
+
+
+def matrix(rng, rows, cols, dt, dist="uniform", order="F"):
+    """One rows x cols matrix of storage datatype ``dt`` ('s','d','c','z')."""
+    re = _component(rng, (rows, cols), dist)
+    if is_complex(dt):
+        im = _component(rng, (rows, cols), dist)
+        val = re + 1j * im
+    else:
+        val = re
+    return np.asarray(val, dtype=NP_OF_DT[dt], order=order)
+
+
+def problem(seed, combo, m, n, k, dist="uniform", transa="n", transb="n",
+            order_a="F", order_b="F", order_c="F"):
+    """Inputs of one gemm: returns (A, B, C) numpy arrays in their stored shapes.
+
+    A is stored m x k (k x m for trans 't'/'h'); B is stored k x n (n x k for 't'/'h').
+    """
+    dc, da, db = combo[0], combo[1], combo[2]
+    rng = np.random.default_rng(seed)
+    a_shape = (k, m) if transa in ("t", "h") else (m, k)
+    b_shape = (n, k) if transb in ("t", "h") else (k, n)
+    # fill order A.re, A.im, B.re, B.im, C.re, C.im
+    A = matrix(rng, *a_shape, da, dist, order_a)
+    B = matrix(rng, *b_shape, db, dist, order_b)
+    C = matrix(rng, m, n, dc, dist, order_c)
+    return A, B, C
+
+
+def torch_matrix(gen, rows, cols, dt, device, low=-1.0, high=1.0):
+    """Device-side uniform matrix, column-major (stored as the transpose of a row-major
+    cols x rows tensor). Used for the large benchmark inputs, which are checked
+    against the oracle on sampled blocks copied back to the host."""
+    import torch
+    tdt = {"s": torch.float32, "d": torch.float64,
+           "c": torch.complex64, "z": torch.complex128}[dt]
+    real = torch.float64 if dt in ("d", "z") else torch.float32
+    ncomp = 2 if is_complex(dt) else 1
+    raw = torch.empty((cols, rows, ncomp), dtype=real, device=device)
+    raw.uniform_(low, high, generator=gen)
+    if ncomp == 2:
+        t = torch.view_as_complex(raw)
+    else:
+        t = raw[..., 0]
+    assert t.dtype == tdt
+    return t.t()  # rows x cols view with unit row stride

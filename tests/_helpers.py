@@ -1,0 +1,59 @@
+"""Shared test helpers: tolerance (normwise error bound) and operand norms.
+
+The bound is  ||C_gpu - C_ref||_F / (|alpha| ||A~||_F ||B~||_F + |beta| ||C||_F)
+              <= 4 k u_x + 4 u_C
+u_x is the unit roundoff of the computation precision (2^-24 single, 2^-53 double),
+u_C that of C's storage precision. The 4 k u_x term bounds the length-k (or 2k, for
+the 1m / 1r layouts) accumulation; the 4 u_C term bounds the epilogue's roundings in
+C's storage precision (beta*C with complex beta: two products and a sum; the cast of
+alpha*AB; the final sum). A~ and B~ are the operands as they enter the product:
+Re(A) when C and B are real, Re(B) when C and A are real, else the full operand.
+"""
+import numpy as np
+
+U = {"s": 2.0 ** -24, "d": 2.0 ** -53}
+
+
+def prec_of(dt):
+    return "d" if dt in ("d", "z") else "s"
+
+
+def is_complex(dt):
+    return dt in ("c", "z")
+
+
+def comp_prec(combo):
+    x = combo[3]
+    return prec_of(combo[0]) if x == "c" else x
+
+
+def op(X, trans):
+    X = np.asarray(X).astype(np.complex128)
+    if trans in ("t", "h"):
+        X = X.T
+    if trans in ("c", "h"):
+        X = np.conj(X)
+    return X
+
+
+def tolerance(combo, k):
+    return 4.0 * max(k, 1) * U[comp_prec(combo)] + 4.0 * U[prec_of(combo[0])]
+
+
+def entering_norms(combo, A, B, transa="n", transb="n"):
+    dc, da, db = combo[0], combo[1], combo[2]
+    Ae, Be = op(A, transa), op(B, transb)
+    if not is_complex(dc) and not is_complex(db):
+        Ae = Ae.real
+    if not is_complex(dc) and not is_complex(da):
+        Be = Be.real
+    return float(np.linalg.norm(Ae)), float(np.linalg.norm(Be))
+
+
+def normwise_error(combo, C_gpu, C_ref, A, B, C_in, alpha, beta, transa="n", transb="n"):
+    """Return (err, bound-denominator) for C_gpu against the oracle's unrounded C_ref."""
+    na, nb = entering_norms(combo, A, B, transa, transb)
+    den = abs(alpha) * na * nb + abs(beta) * float(np.linalg.norm(np.asarray(C_in).astype(np.complex128)))
+    diff = np.asarray(C_gpu).astype(np.complex128) - np.asarray(C_ref)
+    num = float(np.linalg.norm(diff))
+    return (num / den if den > 0 else num), den
