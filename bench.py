@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of mixed-datatype gemm on GB300: C := beta*C + alpha*A*B.
+
+Default workload ("plain_large"): m = n = k = 8192, column-major, no transpose,
+entries U[-1, 1], alpha = beta = 1, the plain cast-then-gemm form (FP32 FFMA for
+single computation precision, FP64 DMMA for double). One step = 16 gemms: the 8
+domain cases of Fig. "mixeddom" x the 2 computation precisions, with the storage
+precisions of (C, A, B) = pattern (step mod 8), so 8 consecutive steps cover all
+128 combinations. Flops are counted as 2mnk x R (R = real products of the case).
+
+Prints ONE JSON line (rank 0). --impl reference times the oracle (CPU) instead.
+"""
+import argparse
+import hashlib
+import itertools
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mixed-dt gemm GFLOPS & %peak per combo; grouped/served req/s, p99 vs plain"
+CASES = list(itertools.product([0, 1], repeat=3))           # (C, A, B) complex?
+PATTERNS = list(itertools.product("sd", repeat=3))           # (C, A, B) precision
+R_OF = {(0, 0, 0): 1, (0, 0, 1): 1, (0, 1, 0): 1, (0, 1, 1): 2,
+        (1, 0, 0): 1, (1, 0, 1): 2, (1, 1, 0): 2, (1, 1, 1): 4}
+NOMINAL_BF16_TFLOPS = 2250.0
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def dt_of(cplx, prec):
+    return ("c" if prec == "s" else "z") if cplx else prec
+
+
+def step_combos(step):
+    pc, pa, pb = PATTERNS[step % 8]
+    out = []
+    for (cc, ac, bc) in CASES:
+        for x in "sd":
+            out.append((dt_of(cc, pc) + dt_of(ac, pa) + dt_of(bc, pb) + x, R_OF[(cc, ac, bc)]))
+    return out
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gemm_simt.cu", "epilogue.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1901_06015_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kernel)
+    except Exception:
+        return None
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch_at_bench_size")
+
+
+# ------------------------------------------------------------------ CPU (oracle) arm
+def oracle_sample(step, n, bm, bn, seed=123):
+    """Time the oracle on one bm x bn block of C (full k = n) for each of the step's
+    16 combos. Returns (useful flops, seconds, threads)."""
+    import numpy as np
+    import oracle
+    from paper_1901_06015_gb300 import synth
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed + step)
+    flops, secs = 0.0, 0.0
+    for combo, R in step_combos(step):
+        A = synth.matrix(rng, bm, n, combo[1])
+        B = synth.matrix(rng, n, bn, combo[2])
+        C = synth.matrix(rng, bm, bn, combo[0])
+        t0 = time.perf_counter()
+        oracle.oracle_mxgemm("n", "n", 1.0, A, B, 1.0, C, comp=combo[3], nthreads=threads)
+        secs += time.perf_counter() - t0
+        flops += 2.0 * bm * bn * n * R
+    return flops, secs, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.size
+    for w in range(args.warmup):
+        oracle_sample(w, n, 64, 64)
+    fl, secs = 0.0, 0.0
+    for s in range(args.steps):
+        f, t, threads = oracle_sample(s, n, 64, 64)
+        fl += f
+        secs += t
+    gf = fl / secs / 1e9
+    sample = f"one 64x64 block of C (k={n}) per gemm of each step (16 gemms), oracle in binary64 with compensated sums"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": gf, "unit": "GFLOPS", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gf, "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"plain_large: 16 mixed-datatype gemms per step (8 domain cases x 2 computation "
+                        f"precisions; storage precisions rotate with the step, 8 steps = all 128 combos), "
+                        f"m=n=k={args.size}, column-major, no transpose, U[-1,1], alpha=beta=1",
+            "m": args.size, "n": args.size, "k": args.size,
+            "single_method": "ffma", "double_method": args.double_method,
+            "l2": "inputs larger than L2 (every operand >= 268 MB at 8192^2), no flush"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import paper_1901_06015_gb300 as mx
+    from paper_1901_06015_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    n = args.size
+    stream = torch.cuda.current_stream()
+
+    # one handle per computation precision so the contraction time of each method is
+    # measured separately (same stream)
+    hs, hd = mx.Handle(), mx.Handle()
+    for h in (hs, hd):
+        h.set_stream(stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    mats = {}
+
+    def mat(role, dt):
+        if (role, dt) not in mats:
+            mats[(role, dt)] = synth.torch_matrix(gen, n, n, dt, dev)
+        return mats[(role, dt)]
+
+    for s in range(8):
+        for combo, _ in step_combos(s):
+            mat("A", combo[1]); mat("B", combo[2]); mat("C", combo[0])
+
+    # load every kernel once on a small problem (lazy module loading stays out of the timing)
+    small = {dt: synth.torch_matrix(gen, 64, 64, dt, dev) for dt in "sdcz"}
+    for s in range(8):
+        for combo, _ in step_combos(s):
+            h, meth = (hs, "ffma") if combo[3] == "s" else (hd, args.double_method)
+            mx.mxgemm_ex(h, meth, "n", "n", 1.0, small[combo[1]], small[combo[2]], 1.0,
+                         small[combo[0]].clone(), comp=combo[3])
+    torch.cuda.synchronize()
+
+    def run_step(step, per_call=None):
+        launches = 0
+        for combo, R in step_combos(step):
+            h, meth = (hs, "ffma") if combo[3] == "s" else (hd, args.double_method)
+            if per_call is not None:
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            mx.mxgemm_ex(h, meth, "n", "n", 1.0, mat("A", combo[1]), mat("B", combo[2]), 1.0,
+                         mat("C", combo[0]), comp=combo[3])
+            launches += 3
+            if per_call is not None:
+                e1.record(stream)
+                per_call.append((combo, R, e0, e1))
+        return launches
+
+    for w in range(args.warmup):
+        run_step(w)
+    torch.cuda.synchronize()
+    for h in (hs, hd):
+        h.set_phase_timing(True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    per_call = []
+    ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for t in range(args.steps):
+        launches += run_step(t, per_call)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    pack_s, con_s, nl_s = hs.phase_times()
+    pack_d, con_d, nl_d = hd.phase_times()
+    for h in (hs, hd):
+        h.set_phase_timing(False)
+
+    flops_step = sum(2.0 * n ** 3 * R for _, R in step_combos(0))
+    my_flops = flops_step * args.steps
+    t_max = ms
+    tot_flops = my_flops
+    if dist is not None:
+        tt = torch.tensor([ms, my_flops], dtype=torch.float64, device=dev)
+        mx_t = tt.clone(); dist.all_reduce(mx_t[:1], op=dist.ReduceOp.MAX)
+        sm_f = tt.clone(); dist.all_reduce(sm_f[1:], op=dist.ReduceOp.SUM)
+        t_max, tot_flops = float(mx_t[0]), float(sm_f[1])
+    value = tot_flops / (t_max / 1e3) / 1e9
+
+    # per-combo GFLOPS (this rank)
+    per_combo = {}
+    for combo, R, e0, e1 in per_call:
+        cms = e0.elapsed_time(e1)
+        per_combo[combo] = round(2.0 * n ** 3 * R / (cms / 1e3) / 1e9, 1)
+
+    peaks, peak_src = measured_peaks()
+    # dominant kernel: the double-precision contraction (nearly all of the step's time)
+    d_flops = sum(2.0 * n ** 3 * R for c, R in step_combos(0) if c[3] == "d") * args.steps
+    s_flops = sum(2.0 * n ** 3 * R for c, R in step_combos(0) if c[3] == "s") * args.steps
+    fp64_peak = peaks["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+    ach_d = d_flops / nl_d / (con_d / nl_d / 1e3) / 1e12 if nl_d else None
+    ach_s = s_flops / nl_s / (con_s / nl_s / 1e3) / 1e12 if nl_s else None
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    ffma_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    kname = "dmma_gemm" if args.double_method == "dmma" else "simt_gemm<double>"
+    roofline = {
+        "kernel": kname, "bound": "tensor", "achieved": ach_d, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": (ach_d / fp64_peak) if ach_d else None,
+        "traffic": traffic_per_launch(kname),
+        "peak_source": f"{peak_src} bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250); "
+                       "kernel timed inside a long step",
+        "share_of_step": con_d / ms if ms else None,
+        "per_launch": "achieved = mean useful flops (2mnk R) per launch / mean contraction-kernel "
+                      "duration, CUDA events around each contraction launch on its stream",
+    }
+    secondary = {"kernel": "simt_gemm<float> (FFMA)", "bound": "alu", "achieved": ach_s, "peak": ffma_peak,
+                 "unit": "TFLOP/s", "frac": (ach_s / ffma_peak) if ach_s else None,
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
+                 "share_of_step": con_s / ms if ms else None}
+    pack_share = (pack_s + pack_d) / ms if ms else None
+
+    # e2e through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = {key: t.cpu().pin_memory() for key, t in mats.items()}
+        out = {dt: torch.empty_like(mats[("C", dt)], device="cpu").pin_memory() for dt in "sdcz"
+               if ("C", dt) in mats}
+        torch.cuda.synchronize()
+        h2d = d2h = 0
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(args.steps):
+            for combo, R in step_combos(t):
+                dA, dB, dC = mat("A", combo[1]), mat("B", combo[2]), mat("C", combo[0])
+                dA.copy_(host[("A", combo[1])], non_blocking=True)
+                dB.copy_(host[("B", combo[2])], non_blocking=True)
+                dC.copy_(host[("C", combo[0])], non_blocking=True)
+                h2d += sum(x.numel() * x.element_size() for x in (dA, dB, dC))
+                h, meth = (hs, "ffma") if combo[3] == "s" else (hd, args.double_method)
+                mx.mxgemm_ex(h, meth, "n", "n", 1.0, dA, dB, 1.0, dC, comp=combo[3])
+                out[combo[0]].copy_(dC, non_blocking=True)
+                d2h += dC.numel() * dC.element_size()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            tt = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt[0])
+        e2e = {"value": tot_flops / (ems / 1e3) / 1e9, "unit": "GFLOPS",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        f, t, threads = oracle_sample(0, n, 128, 128)
+        cpu = {"value": f / t / 1e9, "unit": "GFLOPS", "cores": threads, "kind": "oracle",
+               "sample": f"one 128x128 block of C (k={n}) for each of the step's 16 gemms; "
+                         f"{t:.1f} s of oracle time"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic", "config": workload_config(args),
+            "roofline": roofline, "roofline_single": secondary, "pack_share_of_step": pack_share,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "per_combo_gflops": per_combo,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--double-method", default="dmma", choices=["dmma", "dfma"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * mxgemm -- mixed-datatype general matrix multiplication on one GB300 GPU.
+ *
+ *     C := beta * C + alpha * op(A) * op(B)
+ *
+ * following Van Zee, Parikh and van de Geijn, "Supporting mixed-datatype matrix
+ * multiplication within the BLIS framework" (arXiv 1901.06015). Each of A, B and C
+ * is stored independently as single or double precision, real or complex; the
+ * computation precision is chosen separately (4 x 4 x 4 storage datatypes x 2
+ * computation precisions = 128 combinations).
+ *
+ * Semantics (the same for every entry point below):
+ *  - Domains (Sec. 4.2, Fig. "mixeddom"): real operands behave as complex with zero
+ *    imaginary part, the product P = op(A) op(B) is formed, and
+ *        C real:    C := Re(beta) C + Re(alpha) Re(P)
+ *        C complex: C := beta C + alpha P
+ *    so with C real the imaginary parts that cannot reach C are never computed on
+ *    (cases 1a, 1b, 2ab), and with A and B real only Re(C) receives the product
+ *    while Im(C) is only scaled by beta (case 1c).
+ *  - Precision (Sec. 5.1): A and B are cast to the computation precision (their
+ *    "target datatype": own domain, computation precision) and the whole length-k
+ *    sum is accumulated in it; the result is cast to C's storage precision when it
+ *    is accumulated into C (Sec. 5.1.3, Sec. 6.3).
+ *  - Scalars (Sec. 7.1, option 1 for both): alpha is cast to the computation
+ *    precision, beta to C's storage precision, and alpha*AB is cast to C's precision
+ *    before beta*C is added in C's precision. Sec. 7.2: complex beta is projected when
+ *    C is real; complex alpha is projected in case 0, honoured in case 3, and a
+ *    non-zero Im(alpha) is rejected (MXG_ECOMPLEX_ALPHA) in cases 1a, 1b, 1c, 2ab,
+ *    2ac, 2bc. Rounding is round-to-nearest-even.
+ *  - beta == 0: C is not read (NaN in C does not propagate). alpha == 0 (after the
+ *    cast to the computation precision) or k == 0: A and B are not read and
+ *    C := beta C. m == 0 or n == 0: nothing happens.
+ *
+ * Storage (Sec. 2.2.1, Sec. 3 Fig. "hypoapi"): element (i, j) of a stored matrix X
+ * lives at X + (i * rs + j * cs) elements of X's datatype; a complex element is one
+ * unit (real part first, then imaginary). Strides are in elements, >= 1 for every
+ * dimension longer than 1: column-major (rs = 1), row-major (cs = 1) and general
+ * storage are all accepted for each operand independently. op(A) is m x k; A is
+ * stored k x m when transa is MXG_TRANS or MXG_CONJTRANS (induced transposition,
+ * Sec. 2.2.2). MXG_CONJ conjugates without transposing (Sec. 2.2.3). C must not
+ * overlap itself; A and B may alias each other but not C.
+ *
+ * Ownership and ordering: the caller owns A, B and C (device memory). Work is
+ * enqueued on the handle's stream and is asynchronous; no pointer is kept after the
+ * call's work has passed on that stream. Errors are returned as status codes; no
+ * entry point aborts or throws.
+ */
+#ifndef MXGEMM_H
+#define MXGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage datatypes (Sec. 3: domain x precision). */
+enum { MXG_S = 0, MXG_D = 1, MXG_C = 2, MXG_Z = 3 };
+
+/* Transposition values (Sec. 3, incl. conjugation without transposition). */
+enum { MXG_NOTRANS = 0, MXG_TRANS = 1, MXG_CONJ = 2, MXG_CONJTRANS = 3 };
+
+/* Computation precision (Sec. 5.1.1). MXG_PREC_OF_C: that of C's storage. */
+enum { MXG_PREC_S = 0, MXG_PREC_D = 1, MXG_PREC_OF_C = 2 };
+
+/* Contraction methods. FFMA: plain FP32 fused multiply-add (single);
+ * TF32X3 / BF16X3: split-precision tensor-core products hi*hi + hi*lo + lo*hi with
+ * FP32 accumulation (single); DMMA: FP64 tensor-core mma (double); DFMA: plain FP64
+ * fused multiply-add (double). AUTO picks the fastest method of the precision. */
+enum {
+  MXG_METHOD_AUTO = 0,
+  MXG_METHOD_FFMA = 1,
+  MXG_METHOD_TF32X3 = 2,
+  MXG_METHOD_BF16X3 = 3,
+  MXG_METHOD_DMMA = 4,
+  MXG_METHOD_DFMA = 5
+};
+
+/* Status codes. */
+enum {
+  MXG_OK = 0,
+  MXG_EINVAL = 1,          /* bad enum, negative size, null pointer with work to do,
+                              stride < 1 on a dimension longer than 1, C overlapping
+                              itself, method not of the computation precision */
+  MXG_ECOMPLEX_ALPHA = 2,  /* Im(alpha) != 0 in case 1a, 1b, 1c, 2ab, 2ac or 2bc (Sec. 7.2) */
+  MXG_ENOMEM = 3,          /* workspace allocation failed or caller workspace too small */
+  MXG_ECUDA = 4,           /* a CUDA runtime call failed (see mxg_last_cuda_error) */
+  MXG_ETIMEOUT = 5,        /* a device-side wait ran out of its iteration limit */
+  MXG_ENOTSUP = 6          /* method not available on this device */
+};
+
+/* Domain cases of Fig. "mixeddom", as returned in mxg_plan_info.domain_case:
+ * index = 4*[C complex] + 2*[A complex] + [B complex]. */
+enum {
+  MXG_CASE_0 = 0, MXG_CASE_1B = 1, MXG_CASE_1A = 2, MXG_CASE_2AB = 3,
+  MXG_CASE_1C = 4, MXG_CASE_2BC = 5, MXG_CASE_2AC = 6, MXG_CASE_3 = 7
+};
+
+typedef struct mxg_context* mxg_handle;
+
+/* Description of the real gemm a call reduces to (host-side planning only). */
+typedef struct {
+  int domain_case;          /* MXG_CASE_* (Fig. "mixeddom") */
+  int comp_prec;            /* resolved computation precision: MXG_PREC_S or MXG_PREC_D */
+  int method;               /* resolved MXG_METHOD_* */
+  int whole_op_transposed;  /* 1 if computed as C^T := op(B)^T op(A)^T (Sec. 2.2.5) */
+  int64_t Mr, Nr, Kr;       /* dimensions of the real product (M', N', K') */
+  int real_products;        /* R = M'N'K' / (mnk): 1, 2 or 4 (flops = 2mnk R) */
+  double flops;             /* useful flops 2*m*n*k*R (Fig. "mixeddom") */
+  size_t workspace_bytes;   /* device workspace the call needs (packed operands) */
+} mxg_plan_info;
+
+/*
+ * mxgemm: the mixed-datatype gemm of Sec. 3 Fig. "hypoapi", with domain and
+ * precision folded into one datatype code per operand (dtX in MXG_S..MXG_Z) and the
+ * computation precision precAB as comp_prec. Runs on the calling thread's current
+ * device, on the default (legacy) stream, with a library-owned workspace that grows
+ * as needed. Pointers are device pointers. Returns MXG_OK or an error status; on an
+ * error nothing is enqueued and C is unchanged.
+ */
+int mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,
+           double alpha_re, double alpha_im,
+           const void* A, int dtA, int64_t rsA, int64_t csA,
+           const void* B, int dtB, int64_t rsB, int64_t csB,
+           double beta_re, double beta_im,
+           void* C, int dtC, int64_t rsC, int64_t csC,
+           int comp_prec);
+
+/*
+ * mxgemm_ex: as mxgemm, on handle h (its device, stream and workspace) with an
+ * explicit contraction method (MXG_METHOD_*). A method of the other precision than
+ * the resolved computation precision is MXG_EINVAL.
+ */
+int mxgemm_ex(mxg_handle h, int method, int transa, int transb,
+              int64_t m, int64_t n, int64_t k,
+              double alpha_re, double alpha_im,
+              const void* A, int dtA, int64_t rsA, int64_t csA,
+              const void* B, int dtB, int64_t rsB, int64_t csB,
+              double beta_re, double beta_im,
+              void* C, int dtC, int64_t rsC, int64_t csC,
+              int comp_prec);
+
+/*
+ * mxg_plan: validate a call and describe the real gemm it reduces to (domain case,
+ * M', N', K', R, method, workspace). Host only: makes no CUDA call, so it works
+ * without a GPU. Pointers may be NULL here (they are not dereferenced or checked).
+ * Returns the status mxgemm_ex would return for a validation failure, else MXG_OK.
+ */
+int mxg_plan(int method, int transa, int transb, int64_t m, int64_t n, int64_t k,
+             double alpha_re, double alpha_im,
+             int dtA, int64_t rsA, int64_t csA,
+             int dtB, int64_t rsB, int64_t csB,
+             int dtC, int64_t rsC, int64_t csC,
+             int comp_prec, mxg_plan_info* info);
+
+/* Handles. mxg_create binds the handle to the calling thread's current device and
+ * to the default stream. mxg_destroy frees the library-owned workspace (after
+ * synchronising the handle's stream). */
+int mxg_create(mxg_handle* h);
+int mxg_destroy(mxg_handle h);
+
+/* Stream for subsequent calls on h (a cudaStream_t; NULL = legacy default stream). */
+int mxg_set_stream(mxg_handle h, void* stream);
+
+/* Caller-owned device workspace for subsequent calls on h: ptr must be 256-byte
+ * aligned; a call whose plan needs more than bytes returns MXG_ENOMEM. ptr = NULL
+ * returns to the library-owned, growing workspace. The caller keeps ownership and
+ * must not reuse the memory until work enqueued on h has completed. */
+int mxg_set_workspace(mxg_handle h, void* ptr, size_t bytes);
+
+/* Device error word of h: nonzero if a device-side wait ran out of its iteration
+ * limit since the last call to this function (which clears it). Synchronises h's
+ * stream. Returns MXG_OK or MXG_ECUDA; *flag receives the word. */
+int mxg_check_device_error(mxg_handle h, int* flag);
+
+/* Phase timing on h (tracing). When on, every call on h records CUDA events on h's
+ * stream before its pack launches, between the packs and the contraction launch, and
+ * after the contraction. mxg_phase_times synchronises h's stream, returns the summed
+ * milliseconds of the pack phase and of the contraction phase (the contraction kernel
+ * with its fused epilogue) and the number of contraction launches recorded since the
+ * last query, then forgets them. Turning timing off also forgets them. */
+int mxg_set_phase_timing(mxg_handle h, int on);
+int mxg_phase_times(mxg_handle h, double* pack_ms, double* contraction_ms, int64_t* launches);
+
+/* Human-readable text of a status code (static storage). */
+const char* mxg_strerror(int status);
+
+/* The last CUDA runtime error code seen by the library on this thread (0 if none). */
+int mxg_last_cuda_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int mxg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MXGEMM_H */

@@ -1,0 +1,90 @@
+// Internal declarations shared by the host planner (api.cpp) and the CUDA kernels.
+// Not part of the public C ABI (include/mxgemm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mxg {
+
+// How one logical operand element x = xr + i*xi (already cast to the computation
+// precision and conjugated if requested) is laid out in the packed real operand.
+// The packed operand is a real (K' x MN') matrix; fk/fm are the factors by which a
+// pattern expands K and MN.
+//   RE        1x1: xr                     (real operand, or Re of a complex one:
+//                                           cases 0, 1a, 1b, 1c, and the real side
+//                                           of 2ac / 2bc)
+//   SPLIT_MN  1x2: [xr, xi] along MN       (complex side of 2ac and 2bc: C and the
+//                                           operand viewed as real 2m x n / k x 2n,
+//                                           Sec. 4.2.5)
+//   SPLIT_K   2x1: [xr; xi] along K        (the 1r format of the 1m method, Sec. 4.1;
+//                                           with conj toggled on B it gives case 2ab,
+//                                           Sec. 4.2.3)
+//   ONE_E     2x2: K-row 0 [xr, xi], K-row 1 [-xi, xr]
+//                                          (the 1e format of the 1m method, Eq. (1)
+//                                           for A, Eq. (2) for B)
+enum PackPattern : int { PAT_RE = 0, PAT_SPLIT_MN = 1, PAT_SPLIT_K = 2, PAT_ONE_E = 3 };
+
+inline int pat_fk(int p) { return (p == PAT_SPLIT_K || p == PAT_ONE_E) ? 2 : 1; }
+inline int pat_fm(int p) { return (p == PAT_SPLIT_MN || p == PAT_ONE_E) ? 2 : 1; }
+
+// How the real product P (M' x N') maps onto C.
+//   OUT_REAL    C real: C(i,j) <- P(i,j)                  (cases 0, 1a, 1b, 2ab)
+//   OUT_RE_ONLY C complex, P real: Re C(i,j) <- P(i,j);   (case 1c)
+//               Im C(i,j) only scaled by beta
+//   OUT_ROWPAIR C complex: C(i,j) <- P(2i,j) + i P(2i+1,j) (case 2ac; case 3 by Eq. (1))
+//   OUT_COLPAIR C complex: C(i,j) <- P(i,2j) + i P(i,2j+1) (case 2bc; case 3 by Eq. (2))
+enum OutMode : int { OUT_REAL = 0, OUT_RE_ONLY = 1, OUT_ROWPAIR = 2, OUT_COLPAIR = 3 };
+
+// Layout of a packed operand: MN-major (element (kk, mm) at kk*ld + mm) for the SIMT
+// kernels, K-major (element (kk, mm) at mm*ld + kk) for the tensor-core kernels.
+enum PackLayout : int { LAYOUT_MN_MAJOR = 0, LAYOUT_K_MAJOR = 1 };
+
+// Split formats written by the pack for the split-precision tensor-core methods.
+enum SplitKind : int { SPLIT_NONE = 0, SPLIT_TF32 = 1, SPLIT_BF16 = 2 };
+
+struct PackArgs {
+  const void* src;   // source operand, storage datatype src_dt
+  int src_dt;        // MXG_S..MXG_Z
+  int64_t smn, sk;   // strides (elements) of logical element (mn, p) of op(X): src + mn*smn + p*sk
+  int64_t MN, K;     // logical extent
+  int pattern;       // PackPattern
+  int conj;          // negate the imaginary part before applying the pattern
+  void* dst;         // packed operand (hi plane for split formats)
+  void* dst_lo;      // lo plane for split formats (else unused)
+  int64_t ld;        // leading dimension of dst (elements)
+  int64_t MNp, Kp;   // padded extent of the packed operand (written in full, zero padding)
+  int layout;        // PackLayout
+  int split;         // SplitKind
+};
+
+struct EpiArgs {
+  void* C;           // C after the optional whole-op transpose
+  int64_t rs, cs;    // strides of C (elements)
+  int64_t m, n;      // extent of C
+  double ar, ai;     // alpha, already rounded to the computation precision
+  double br, bi;     // beta, already rounded to C's storage precision
+  int beta_zero;     // C is not read
+};
+
+struct GemmArgs {
+  const void* A;     // packed A' (comp precision), MN-major, Kp x lda
+  const void* B;     // packed B', MN-major, Kp x ldb
+  int64_t lda, ldb;  // = padded M', N'
+  int64_t Kp;        // padded K' (multiple of the kernel's k tile)
+  int64_t Mp, Np;    // padded M', N' (multiples of the kernel's tile)
+  EpiArgs e;
+};
+
+// Tile sizes the planner pads to, per method.
+struct TileCfg { int tm, tn, tk; };
+TileCfg tile_cfg(int method);
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_pack(const PackArgs& a, int comp_double, cudaStream_t s);
+cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_scale_c(const EpiArgs& e, int c_dt, cudaStream_t s);
+
+}  // namespace mxg

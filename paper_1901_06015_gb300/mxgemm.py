@@ -1,0 +1,239 @@
+"""ctypes binding of the C ABI in ``include/mxgemm.h`` (argument marshalling only).
+
+Every computation happens in the CUDA library; this module turns torch tensors into
+(pointer, datatype code, row stride, column stride) and Python scalars into
+(re, im) pairs. Tensors are passed as stored: for trans 't'/'h', A is the stored
+k x m matrix and B the stored n x k matrix.
+"""
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+DT_CODES = {"s": 0, "d": 1, "c": 2, "z": 3}
+TRANS_CODES = {"n": 0, "t": 1, "c": 2, "h": 3}
+PREC_CODES = {"s": 0, "d": 1, "c": 2}  # 'c': the precision of C
+METHODS = {"auto": 0, "ffma": 1, "tf32x3": 2, "bf16x3": 3, "dmma": 4, "dfma": 5}
+CASE_NAMES = ["0", "1b", "1a", "2ab", "1c", "2bc", "2ac", "3"]
+
+_i32, _i64, _dbl, _vp, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_lock = threading.Lock()
+_lib = None
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("domain_case", _i32), ("comp_prec", _i32), ("method", _i32),
+                ("whole_op_transposed", _i32), ("Mr", _i64), ("Nr", _i64), ("Kr", _i64),
+                ("real_products", _i32), ("flops", _dbl), ("workspace_bytes", _sz)]
+
+
+class MxgError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {mxg_strerror(status)} (status {status})")
+
+
+_GEMM_TAIL = [_i32, _i32, _i64, _i64, _i64, _dbl, _dbl, _vp, _i32, _i64, _i64,
+              _vp, _i32, _i64, _i64, _dbl, _dbl, _vp, _i32, _i64, _i64, _i32]
+
+
+def lib():
+    """Load the CUDA library, building it in-tree first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            L.mxgemm.restype = _i32
+            L.mxgemm.argtypes = _GEMM_TAIL
+            L.mxgemm_ex.restype = _i32
+            L.mxgemm_ex.argtypes = [_vp, _i32] + _GEMM_TAIL
+            L.mxg_plan.restype = _i32
+            L.mxg_plan.argtypes = [_i32, _i32, _i32, _i64, _i64, _i64, _dbl, _dbl,
+                                   _i32, _i64, _i64, _i32, _i64, _i64, _i32, _i64, _i64,
+                                   _i32, ctypes.POINTER(PlanInfo)]
+            L.mxg_create.restype = _i32
+            L.mxg_create.argtypes = [ctypes.POINTER(_vp)]
+            L.mxg_destroy.restype = _i32
+            L.mxg_destroy.argtypes = [_vp]
+            L.mxg_set_stream.restype = _i32
+            L.mxg_set_stream.argtypes = [_vp, _vp]
+            L.mxg_set_workspace.restype = _i32
+            L.mxg_set_workspace.argtypes = [_vp, _vp, _sz]
+            L.mxg_check_device_error.restype = _i32
+            L.mxg_check_device_error.argtypes = [_vp, ctypes.POINTER(_i32)]
+            L.mxg_set_phase_timing.restype = _i32
+            L.mxg_set_phase_timing.argtypes = [_vp, _i32]
+            L.mxg_phase_times.restype = _i32
+            L.mxg_phase_times.argtypes = [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]
+            L.mxg_strerror.restype = ctypes.c_char_p
+            L.mxg_strerror.argtypes = [_i32]
+            L.mxg_last_cuda_error.restype = _i32
+            L.mxg_version.restype = _i32
+            _lib = L
+    return _lib
+
+
+def mxg_strerror(status):
+    return lib().mxg_strerror(int(status)).decode()
+
+
+def dt_of(t):
+    import torch
+    m = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _mat(t):
+    if t.dim() != 2:
+        raise ValueError("matrices must be 2-D tensors")
+    rs, cs = t.stride()
+    return ctypes.c_void_p(t.data_ptr()), DT_CODES[dt_of(t)], int(rs), int(cs)
+
+
+def _dims(transa, transb, A, C):
+    m, n = C.shape
+    k = A.shape[0] if transa in ("t", "h") else A.shape[1]
+    return int(m), int(n), int(k)
+
+
+def _scalars(alpha, beta):
+    a, b = complex(alpha), complex(beta)
+    return a.real, a.imag, b.real, b.imag
+
+
+def _args(transa, transb, alpha, A, B, beta, C, comp):
+    m, n, k = _dims(transa, transb, A, C)
+    ar, ai, br, bi = _scalars(alpha, beta)
+    pa, da, rsa, csa = _mat(A)
+    pb, db, rsb, csb = _mat(B)
+    pc, dc, rsc, csc = _mat(C)
+    return (TRANS_CODES[transa], TRANS_CODES[transb], m, n, k, ar, ai,
+            pa, da, rsa, csa, pb, db, rsb, csb, br, bi, pc, dc, rsc, csc, PREC_CODES[comp])
+
+
+def mxgemm(transa, transb, alpha, A, B, beta, C, comp="c"):
+    """C := beta*C + alpha*op(A)*op(B) through the C entry point ``mxgemm`` (current
+    device, legacy default stream, library-owned workspace). Raises MxgError."""
+    st = lib().mxgemm(*_args(transa, transb, alpha, A, B, beta, C, comp))
+    if st:
+        raise MxgError(st, "mxgemm")
+    return C
+
+
+class Handle:
+    """An ``mxg_handle``: device, stream and workspace for ``mxgemm_ex``."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        st = lib().mxg_create(ctypes.byref(h))
+        if st:
+            raise MxgError(st, "mxg_create")
+        self.h = h
+        self._ws = None
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        st = lib().mxg_set_stream(self.h, ctypes.c_void_p(ptr or 0))
+        if st:
+            raise MxgError(st, "mxg_set_stream")
+
+    def set_workspace(self, tensor):
+        """Caller-owned workspace (a CUDA tensor kept alive by the handle), or None."""
+        if tensor is None:
+            st = lib().mxg_set_workspace(self.h, None, 0)
+        else:
+            st = lib().mxg_set_workspace(self.h, ctypes.c_void_p(tensor.data_ptr()),
+                                         tensor.numel() * tensor.element_size())
+        if st:
+            raise MxgError(st, "mxg_set_workspace")
+        self._ws = tensor
+
+    def check_device_error(self):
+        f = _i32(0)
+        st = lib().mxg_check_device_error(self.h, ctypes.byref(f))
+        if st:
+            raise MxgError(st, "mxg_check_device_error")
+        return int(f.value)
+
+    def set_phase_timing(self, on):
+        st = lib().mxg_set_phase_timing(self.h, 1 if on else 0)
+        if st:
+            raise MxgError(st, "mxg_set_phase_timing")
+
+    def phase_times(self):
+        """(pack_ms, contraction_ms, contraction_launches) since the last query."""
+        a, b, n = _dbl(0), _dbl(0), _i64(0)
+        st = lib().mxg_phase_times(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n))
+        if st:
+            raise MxgError(st, "mxg_phase_times")
+        return a.value, b.value, int(n.value)
+
+    def close(self):
+        if self.h:
+            lib().mxg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles = {}
+
+
+def _handle_for_current():
+    import torch
+    dev = torch.cuda.current_device()
+    h = _handles.get(dev)
+    if h is None:
+        h = _handles[dev] = Handle()
+    return h
+
+
+def mxgemm_ex(handle, method, transa, transb, alpha, A, B, beta, C, comp="c", stream=None):
+    """C := beta*C + alpha*op(A)*op(B) through ``mxgemm_ex`` with an explicit method.
+    handle=None uses a per-device handle bound to torch's current stream (or
+    ``stream`` if given)."""
+    import torch
+    if handle is None:
+        handle = _handle_for_current()
+        handle.set_stream(stream if stream is not None else torch.cuda.current_stream())
+    st = lib().mxgemm_ex(handle.h, METHODS[method] if isinstance(method, str) else int(method),
+                         *_args(transa, transb, alpha, A, B, beta, C, comp))
+    if st:
+        raise MxgError(st, "mxgemm_ex")
+    return C
+
+
+def mxg_plan(combo_or_dts, m, n, k, transa="n", transb="n", alpha=1.0, method="auto",
+             strides=None, comp=None):
+    """Host-only planning (no CUDA call): returns PlanInfo or raises MxgError.
+
+    ``combo_or_dts`` is a label 'cabx' (C, A, B datatypes, computation precision
+    's'/'d', or 'c' = precision of C). ``strides`` = ((rsA, csA), (rsB, csB),
+    (rsC, csC)); default column-major."""
+    dc, da, db = combo_or_dts[0], combo_or_dts[1], combo_or_dts[2]
+    x = comp or (combo_or_dts[3] if len(combo_or_dts) > 3 else "c")
+    if strides is None:
+        a_rows = k if transa in ("t", "h") else m
+        b_rows = n if transb in ("t", "h") else k
+        strides = ((1, max(a_rows, 1)), (1, max(b_rows, 1)), (1, max(m, 1)))
+    (rsa, csa), (rsb, csb), (rsc, csc) = strides
+    a = complex(alpha)
+    info = PlanInfo()
+    st = lib().mxg_plan(METHODS[method] if isinstance(method, str) else int(method),
+                        TRANS_CODES[transa], TRANS_CODES[transb], m, n, k, a.real, a.imag,
+                        DT_CODES[da], rsa, csa, DT_CODES[db], rsb, csb, DT_CODES[dc], rsc, csc,
+                        PREC_CODES[x], ctypes.byref(info))
+    if st:
+        raise MxgError(st, "mxg_plan")
+    return info

@@ -1,0 +1,106 @@
+"""CPU-only checks of the C ABI library: it builds, loads, exports every function the
+header declares, and its host-side planner classifies and sizes calls as the paper's
+case table says (no CUDA call is made)."""
+import json
+import os
+import re
+
+import pytest
+
+import paper_1901_06015_gb300 as mx
+from paper_1901_06015_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                                txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = mx.lib()
+    names = _declared_functions()
+    assert "mxgemm" in names and "mxg_plan" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.mxg_version() >= 10000
+
+
+def test_strerror_codes():
+    for st in range(7):
+        assert mx.mxg_strerror(st) and "unknown" not in mx.mxg_strerror(st)
+
+
+def test_case_table_and_real_products_match_figure():
+    g = json.load(open(os.path.join(GOLDEN, "mixeddom.json")))
+    for row in g["cases"]:
+        dc = "z" if row["C"] == "C" else "d"
+        da = "z" if row["A"] == "C" else "d"
+        db = "z" if row["B"] == "C" else "d"
+        for x in "sd":
+            info = mx.mxg_plan(dc + da + db + x, 64, 48, 32)
+            assert mx.CASE_NAMES[info.domain_case] == row["case"]
+            assert 2 * info.real_products == row["flops_per_mnk"]
+            assert info.flops == row["flops_per_mnk"] * 64 * 48 * 32
+            assert info.Mr * info.Nr * info.Kr == info.real_products * 64 * 48 * 32
+            assert info.comp_prec == (0 if x == "s" else 1)
+
+
+def test_comp_precision_defaults_to_C():
+    assert mx.mxg_plan("sddc", 8, 8, 8).comp_prec == 0
+    assert mx.mxg_plan("zccc", 8, 8, 8).comp_prec == 1
+
+
+@pytest.mark.parametrize("combo", synth.all_combos())
+def test_every_combo_plans(combo):
+    info = mx.mxg_plan(combo, 100, 90, 80)
+    assert info.workspace_bytes > 0
+    assert info.method in (1, 4)
+
+
+def test_whole_op_transpose_for_row_major_C():
+    info = mx.mxg_plan("zzsd", 50, 40, 30, strides=((1, 50), (1, 30), (40, 1)))
+    assert info.whole_op_transposed == 1
+    assert mx.CASE_NAMES[info.domain_case] == "2ac"   # reported for the call as given
+    assert (info.Mr, info.Nr, info.Kr) == (40, 100, 30)  # computed as 2bc on C^T
+    info = mx.mxg_plan("zzsd", 50, 40, 30)
+    assert info.whole_op_transposed == 0 and (info.Mr, info.Nr, info.Kr) == (100, 40, 30)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(m=-1), dict(transa="x"), dict(strides=((0, 5), (1, 5), (1, 5))),
+    dict(strides=((1, 5), (1, 5), (1, 1))),        # C overlaps itself
+    dict(method="ffma", comp="d"), dict(method="dmma", comp="s"),
+])
+def test_invalid_arguments(bad):
+    kw = dict(m=5, n=5, k=5, transa="n", transb="n", method="auto", strides=None, comp=None)
+    kw.update(bad)
+    with pytest.raises((mx.MxgError, KeyError)) as e:
+        mx.mxg_plan("dddd", kw["m"], kw["n"], kw["k"], transa=kw["transa"], transb=kw["transb"],
+                    method=kw["method"], strides=kw["strides"], comp=kw["comp"])
+    if isinstance(e.value, mx.MxgError):
+        assert e.value.status == 1
+
+
+@pytest.mark.parametrize("combo", ["sscs", "scss", "zdds", "dzzd", "zszd", "zzsd"])
+def test_imaginary_alpha_status(combo):
+    with pytest.raises(mx.MxgError) as e:
+        mx.mxg_plan(combo, 4, 4, 4, alpha=1 + 1j)
+    assert e.value.status == 2
+    mx.mxg_plan(combo[:3] + combo[3], 4, 4, 4, alpha=2.0)
+    mx.mxg_plan("zzzd", 4, 4, 4, alpha=1 + 1j)
+    mx.mxg_plan("dddd", 4, 4, 4, alpha=1 + 1j)
+
+
+def test_empty_operands_accept_any_strides():
+    # k == 0: A is m x 0 and B is 0 x n; their strides are never used
+    info = mx.mxg_plan("dddd", 5, 4, 0, strides=((1, 0), (0, 0), (1, 5)))
+    assert info.flops == 0

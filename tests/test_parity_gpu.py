@@ -1,0 +1,146 @@
+"""Parity of the CUDA path against the oracle (GPU). Every call goes through the C ABI
+(mxgemm_ex / mxgemm) via the ctypes binding."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle_mxgemm
+from paper_1901_06015_gb300 import synth
+from tests._helpers import normwise_error, tolerance, comp_prec
+from tests.gpu_util import run, methods_for, to_device
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALL = synth.all_combos()
+
+
+def _check(combo, A, B, C0, alpha, beta, ta="n", tb="n", method="auto", k=None):
+    ref_C = C0.copy(order="K") if C0.flags["F_CONTIGUOUS"] or C0.flags["C_CONTIGUOUS"] else np.array(C0)
+    ref = oracle_mxgemm(ta, tb, alpha, A, B, beta, ref_C, comp=combo[3])
+    got = run(combo, A, B, C0, alpha, beta, ta, tb, method)
+    kk = k if k is not None else (A.shape[0] if ta in "th" else A.shape[1])
+    err, _ = normwise_error(combo, got, ref, A, B, C0, alpha, beta, ta, tb)
+    tol = tolerance(combo, kk)
+    assert err <= tol, (combo, method, ta, tb, err, tol)
+    return err
+
+
+@pytest.mark.parametrize("combo", ALL)
+def test_plain_small_all_combos(combo):
+    """All 128 combinations at m = n = k = 128, column-major, no transpose, entries
+    U[-1, 1], alpha = 1.5, beta = -0.5, seed 0 -- for every method of the precision."""
+    A, B, C0 = synth.problem(0, combo, 128, 128, 128)
+    for meth in methods_for(combo):
+        _check(combo, A, B, C0, 1.5, -0.5, method=meth)
+
+
+@pytest.mark.parametrize("combo", ALL)
+def test_small_integers_bit_exact(combo):
+    """Integer entries in [-4, 4]: every product and partial sum is exact in every
+    precision, so the GPU result equals the oracle's rounded result bit for bit.
+    Ragged sizes spanning several tiles, all methods of the precision."""
+    m, n, k = 135, 67, 150
+    A, B, C0 = synth.problem(1, combo, m, n, k, dist="smallint")
+    for (alpha, beta), meth in itertools.product([(1.0, 0.0), (1.5, -0.5), (-2.0, 1.0)], methods_for(combo)):
+        ref_C = C0.copy(order="F")
+        oracle_mxgemm("n", "n", alpha, A, B, beta, ref_C, comp=combo[3])
+        got = run(combo, A, B, C0, alpha, beta, method=meth)
+        assert np.array_equal(got, ref_C), (combo, meth, alpha, beta)
+
+
+def _case_reps():
+    """One combo per (domain case, computation precision), precision pattern rotating."""
+    reps = []
+    pats = [(p, q, r) for p in "sd" for q in "sd" for r in "sd"]
+    for ci, (cd, ad, bd) in enumerate(itertools.product([0, 1], repeat=3)):
+        for xi, x in enumerate("sd"):
+            pc, pa, pb = pats[(ci * 2 + xi) % 8]
+            to = lambda cplx, p: ("c" if p == "s" else "z") if cplx else p
+            reps.append(to(cd, pc) + to(ad, pa) + to(bd, pb) + x)
+    return reps
+
+
+REPS = _case_reps()
+
+
+@pytest.mark.parametrize("combo", REPS)
+def test_trans_and_layouts(combo):
+    """All 16 trans pairs, column/row/general storage of every operand, ragged sizes."""
+    rng = np.random.default_rng(3)
+    for ta, tb in itertools.product("ntch", repeat=2):
+        m, n, k = (int(v) for v in rng.integers(1, 90, size=3))
+        A, B, C0 = synth.problem(int(rng.integers(1 << 30)), combo, m, n, k, transa=ta, transb=tb,
+                                 order_a="FC"[int(rng.integers(2))], order_b="FC"[int(rng.integers(2))],
+                                 order_c="FC"[int(rng.integers(2))])
+        if rng.integers(3) == 0:  # general storage for C
+            big = np.zeros((2 * m + 3, 3 * n + 1), dtype=C0.dtype)
+            view = big[1::2, ::3][:m, :n]
+            view[...] = C0
+            C0 = view
+        alpha = (0.75 - 0.25j) if combo[:3] in ("zzz", "ccc", "zcz", "czc", "zzc", "ccz", "czz", "zcc") or \
+            all(c in "cz" for c in combo[:3]) else 1.25
+        beta = (0.5 + 0.5j) if combo[0] in "cz" else -0.75
+        for meth in methods_for(combo):
+            _check(combo, A, B, C0, alpha, beta, ta, tb, meth)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 9, 3), (17, 1, 5), (5, 6, 1), (129, 130, 131), (255, 33, 7)])
+def test_ragged_shapes(shape):
+    m, n, k = shape
+    for combo in REPS:
+        A, B, C0 = synth.problem(4, combo, m, n, k)
+        alpha = (1.0 + 0.5j) if all(c in "cz" for c in combo[:3]) else 1.5
+        for meth in methods_for(combo):
+            _check(combo, A, B, C0, alpha, -0.5, method=meth)
+
+
+def test_quick_returns_and_scalars():
+    A, B, C0 = synth.problem(5, "zzzd", 40, 30, 20)
+    # k == 0 and alpha == 0: C := beta*C exactly
+    got = run("zzzd", A[:, :0], B[:0, :], C0, 1.5, -0.5)
+    assert np.array_equal(got, (-0.5 * C0).astype(C0.dtype))
+    got = run("zzzd", A, B, C0, 0.0, -0.5)
+    assert np.array_equal(got, (-0.5 * C0).astype(C0.dtype))
+    # beta == 0: C is not read
+    Cn = np.full_like(C0, np.nan)
+    got = run("zzzd", A, B, Cn, 1.0, 0.0)
+    assert np.all(np.isfinite(got))
+    # m == 0: nothing happens
+    run("dddd", np.zeros((0, 3)), np.zeros((3, 4)), np.zeros((0, 4)), 1.0, 1.0)
+
+
+def test_complex_alpha_rejected_and_C_untouched():
+    from paper_1901_06015_gb300 import MxgError, mxgemm_ex
+    A, B, C0 = synth.problem(6, "zdds", 8, 8, 8)
+    dA, dB, dC = to_device(A), to_device(B), to_device(C0)
+    with pytest.raises(MxgError) as e:
+        mxgemm_ex(None, "auto", "n", "n", 1.0 + 0.5j, dA, dB, 1.0, dC, comp="s")
+    assert e.value.status == 2
+    torch.cuda.synchronize()
+    assert np.array_equal(dC.cpu().numpy(), C0)
+
+
+def test_invariants_on_gpu():
+    """1c: Im(C_new) = beta*Im(C) bit for bit; C real ignores Im(A) (1a)."""
+    A, B, C0 = synth.problem(7, "zddd", 50, 40, 30)
+    got = run("zddd", A, B, C0, 2.0, -0.5, method="dmma")
+    assert np.array_equal(got.imag, (-0.5 * C0.imag))
+    A, B, C0 = synth.problem(8, "dzdd", 50, 40, 30)
+    A2 = (A.real - 7j * A.imag).astype(A.dtype)
+    assert np.array_equal(run("dzdd", A, B, C0, 1.5, 0.25), run("dzdd", A2, B, C0, 1.5, 0.25))
+
+
+def test_default_entry_point_mxgemm():
+    """The handle-less C entry point (legacy default stream, library workspace)."""
+    from paper_1901_06015_gb300 import mxgemm
+    A, B, C0 = synth.problem(9, "czsc", 70, 50, 90)
+    ref_C = C0.copy(order="F")
+    ref = oracle_mxgemm("n", "n", 1.5, A, B, -0.5, ref_C, comp="c")
+    dA, dB, dC = to_device(A), to_device(B), to_device(C0)
+    torch.cuda.synchronize()
+    mxgemm("n", "n", 1.5, dA, dB, -0.5, dC, comp="c")
+    torch.cuda.synchronize()
+    err, _ = normwise_error("czsc", dC.cpu().numpy(), ref, A, B, C0, 1.5, -0.5)
+    assert err <= tolerance("czss", 90)
