@@ -54,6 +54,7 @@ static bool strides_ok(int64_t rows, int64_t cols, int64_t rs, int64_t cs) {
 // C must not overlap itself: with the smaller stride's dimension spanning less than
 // the larger stride (the usual sufficient condition for a strided 2-D view).
 static bool no_self_overlap(int64_t m, int64_t n, int64_t rs, int64_t cs) {
+  if (m == 0 || n == 0) return true;
   if (m <= 1 && n <= 1) return true;
   if (m <= 1) return cs >= 1;
   if (n <= 1) return rs >= 1;

@@ -104,3 +104,8 @@ def test_empty_operands_accept_any_strides():
     # k == 0: A is m x 0 and B is 0 x n; their strides are never used
     info = mx.mxg_plan("dddd", 5, 4, 0, strides=((1, 0), (0, 0), (1, 5)))
     assert info.flops == 0
+
+
+def test_empty_C_accepts_any_strides():
+    info = mx.mxg_plan("dddd", 0, 4, 3, strides=((0, 0), (1, 3), (0, 0)))
+    assert info.flops == 0
