@@ -87,7 +87,9 @@ enum {
   MXG_ENOMEM = 3,          /* workspace allocation failed or caller workspace too small */
   MXG_ECUDA = 4,           /* a CUDA runtime call failed (see mxg_last_cuda_error) */
   MXG_ETIMEOUT = 5,        /* a device-side wait ran out of its iteration limit */
-  MXG_ENOTSUP = 6          /* method not available on this device */
+  MXG_ENOTSUP = 6,         /* method not available on this device */
+  MXG_ESCRATCH = 7         /* mxgemm_noalloc: the call needs more scratch than the fixed
+                              MXG_NOALLOC_SCRATCH_BYTES buffer holds */
 };
 
 /* Domain cases of Fig. "mixeddom", as returned in mxg_plan_info.domain_case:
@@ -182,6 +184,36 @@ int mxg_check_device_error(mxg_handle h, int* flag);
  * last query, then forgets them. Turning timing off also forgets them. */
 int mxg_set_phase_timing(mxg_handle h, int on);
 int mxg_phase_times(mxg_handle h, double* pack_ms, double* contraction_ms, int64_t* launches);
+
+/*
+ * mxgemm_noalloc: mxgemm_ex without any device allocation. (The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc:
+ * work enqueued while a stream is captured into a CUDA graph, latency-critical loops
+ * that cannot take the implicit synchronisation of cudaMalloc/cudaFree, and
+ * applications whose device memory is all owned by another allocator.)
+ *
+ * Same arguments and semantics as mxgemm_ex, with a cudaStream_t (NULL = legacy
+ * default stream) in place of the handle. The packed operands live in one fixed
+ * file-scope device array of MXG_NOALLOC_SCRATCH_BYTES bytes, which every GPU that
+ * loads this code holds until the process exits; the call makes no cudaMalloc,
+ * cudaFree or other allocating call. A problem whose packed operands need more than
+ * that (see mxg_plan's workspace_bytes) is rejected with MXG_ESCRATCH and nothing is
+ * enqueued. The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream capture.
+ * All calls in the process share the one array and it keeps the last call's contents
+ * (every call rewrites all of the part it uses, so nothing needs clearing), so calls
+ * whose work may overlap on the GPU -- on different streams, or from several host
+ * threads -- race on it: serialise them on one stream.
+ */
+#define MXG_NOALLOC_SCRATCH_BYTES (32u << 20)
+int mxgemm_noalloc(void* stream, int method, int transa, int transb,
+                   int64_t m, int64_t n, int64_t k,
+                   double alpha_re, double alpha_im,
+                   const void* A, int dtA, int64_t rsA, int64_t csA,
+                   const void* B, int dtB, int64_t rsB, int64_t csB,
+                   double beta_re, double beta_im,
+                   void* C, int dtC, int64_t rsC, int64_t csC,
+                   int comp_prec);
 
 /* Human-readable text of a status code (static storage). */
 const char* mxg_strerror(int status);

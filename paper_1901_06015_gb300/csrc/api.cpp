@@ -294,6 +294,7 @@ const char* mxg_strerror(int status) {
     case MXG_ECUDA: return "CUDA runtime error";
     case MXG_ETIMEOUT: return "device-side wait ran out of its iteration limit";
     case MXG_ENOTSUP: return "method not supported on this device";
+    case MXG_ESCRATCH: return "problem needs more scratch than the fixed no-allocation buffer (MXG_NOALLOC_SCRATCH_BYTES) holds";
   }
   return "unknown status";
 }

@@ -65,6 +65,8 @@ def lib():
             L.mxg_set_workspace.argtypes = [_vp, _vp, _sz]
             L.mxg_check_device_error.restype = _i32
             L.mxg_check_device_error.argtypes = [_vp, ctypes.POINTER(_i32)]
+            L.mxgemm_noalloc.restype = _i32
+            L.mxgemm_noalloc.argtypes = [_vp, _i32] + _GEMM_TAIL
             L.mxg_set_phase_timing.restype = _i32
             L.mxg_set_phase_timing.argtypes = [_vp, _i32]
             L.mxg_phase_times.restype = _i32
@@ -211,6 +213,22 @@ def mxgemm_ex(handle, method, transa, transb, alpha, A, B, beta, C, comp="c", st
                          *_args(transa, transb, alpha, A, B, beta, C, comp))
     if st:
         raise MxgError(st, "mxgemm_ex")
+    return C
+
+
+def mxgemm_noalloc(method, transa, transb, alpha, A, B, beta, C, comp="c", stream=None):
+    """C := beta*C + alpha*op(A)*op(B) through ``mxgemm_noalloc``: no device allocation;
+    the packed operands use the library's fixed scratch array. ``stream`` defaults to
+    torch's current stream. Raises MxgError (status 7 when the problem needs more
+    scratch than the fixed array holds)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ptr = getattr(s, "cuda_stream", s)
+    st = lib().mxgemm_noalloc(ctypes.c_void_p(ptr or 0),
+                              METHODS[method] if isinstance(method, str) else int(method),
+                              *_args(transa, transb, alpha, A, B, beta, C, comp))
+    if st:
+        raise MxgError(st, "mxgemm_noalloc")
     return C
 
 

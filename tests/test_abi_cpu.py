@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_strerror_codes():
-    for st in range(7):
+    for st in range(8):
         assert mx.mxg_strerror(st) and "unknown" not in mx.mxg_strerror(st)
 
 
