@@ -27,7 +27,8 @@
  *       C complex: C_new = beta * C + alpha * P
  *     Imaginary alpha is an error in cases 1a, 1b, 1c, 2ab, 2ac, 2bc (Sec. 7.2); in
  *     case 0 it is dropped (projected), in case 3 it is honoured.
- *     beta == 0 means C is not read (BLAS convention; the paper is silent).
+ *     beta == 0 means C is not read, and alpha == 0 (after its cast) means A and B
+ *     are not read (BLAS conventions; the paper is silent on both).
  *  4. The length-k sums use the compensated dot product Dot2 of Ogita, Rump and
  *     Oishi (SIAM J. Sci. Comput. 26(6), 2005), so the oracle's own error is about
  *     one unit roundoff of binary64 plus O(k u^2).
@@ -137,6 +138,7 @@ int oracle_mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,
         const double ar = rnd_prec(alpha_re, comp), ai = rnd_prec(alpha_im, comp);
         const double br = rnd_prec(beta_re, precC), bi = rnd_prec(beta_im, precC);
         const int beta_zero = (br == 0.0 && bi == 0.0);
+        const int alpha_zero = (ar == 0.0 && ai == 0.0);
         int64_t j;
         (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
@@ -147,7 +149,7 @@ int oracle_mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,
                 double Pre, Pim;
                 zval c = {0.0, 0.0}, cn;
                 dot2_init(&pre); dot2_init(&pim);
-                for (p = 0; p < k; ++p) {
+                for (p = 0; p < (alpha_zero ? 0 : k); ++p) {
                     zval a = load_op(A, dtA, rsA, csA, transa, i, p);
                     zval b = load_op(B, dtB, rsB, csB, transb, p, j);
                     /* cast each component to the computation precision (Sec. 5.1.2) */

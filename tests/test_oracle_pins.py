@@ -353,3 +353,13 @@ def test_case_table_matches_figure():
         da = "z" if row["A"] == "C" else "d"
         db = "z" if row["B"] == "C" else "d"
         assert order[oracle.oracle_case_of(dc, da, db)] == row["case"]
+
+
+def test_alpha_zero_does_not_read_A_and_B():
+    """alpha == 0 (after its cast): C := beta*C and non-finite A or B cannot leak in."""
+    A, B, C0 = synth.problem(12, "zzzs", 4, 5, 6)
+    A[0, 0] = np.nan
+    B[1, 1] = np.inf
+    C1 = C0.copy(order="F")
+    oracle_mxgemm("n", "n", 1e-50, A, B, -0.5, C1, comp="s")   # 1e-50 rounds to 0 in single
+    assert np.array_equal(C1, (-0.5 * C0).astype(C0.dtype))
