@@ -141,9 +141,19 @@ int make_plan(const Call& c, int method, Plan* p) {
   P.Mp = round_up(P.Mr, t.tm);
   P.Np = round_up(P.Nr, t.tn);
   P.Kp = round_up(P.Kr, t.tk);
-  const size_t esz = P.comp_double ? 8 : 4;
-  P.bytes_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
-  P.bytes_b = align256(static_cast<size_t>(P.Kp) * P.Np * esz);
+  if (method == MXG_METHOD_TF32X3 || method == MXG_METHOD_BF16X3) {
+    // two planes (hi, lo) per operand, K-major, for TMA
+    P.split = (method == MXG_METHOD_BF16X3) ? SPLIT_BF16 : SPLIT_TF32;
+    const size_t esz = (P.split == SPLIT_BF16) ? 2 : 4;
+    P.plane_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
+    P.plane_b = align256(static_cast<size_t>(P.Kp) * P.Np * esz);
+    P.bytes_a = 2 * P.plane_a;
+    P.bytes_b = 2 * P.plane_b;
+  } else {
+    const size_t esz = P.comp_double ? 8 : 4;
+    P.bytes_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
+    P.bytes_b = align256(static_cast<size_t>(P.Kp) * P.Np * esz);
+  }
   P.workspace = P.bytes_a + P.bytes_b;
   return MXG_OK;
 }
@@ -165,7 +175,7 @@ EpiArgs plan_epilogue(const Plan& P) {
   return e;
 }
 
-int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid) {
+int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, int* dev_err) {
   if (P.kind == PLAN_NOOP) return MXG_OK;
   if (P.kind == PLAN_SCALE) {
     EpiArgs e = plan_epilogue(P);
@@ -180,6 +190,9 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid) {
   pa.MN = w.m; pa.K = w.k; pa.pattern = P.pat_a; pa.conj = P.conj_a;
   pa.dst = base; pa.dst_lo = nullptr; pa.ld = P.Mp; pa.MNp = P.Mp; pa.Kp = P.Kp;
   pa.layout = LAYOUT_MN_MAJOR; pa.split = SPLIT_NONE;
+  if (P.split != SPLIT_NONE) {
+    pa.dst_lo = base + P.plane_a; pa.ld = P.Kp; pa.layout = LAYOUT_K_MAJOR; pa.split = P.split;
+  }
   int st = cuda_status(launch_pack(pa, P.comp_double, s));
   if (st) return st;
   PackArgs pb{};
@@ -188,9 +201,18 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid) {
   pb.MN = w.n; pb.K = w.k; pb.pattern = P.pat_b; pb.conj = P.conj_b;
   pb.dst = base + P.bytes_a; pb.dst_lo = nullptr; pb.ld = P.Np; pb.MNp = P.Np; pb.Kp = P.Kp;
   pb.layout = LAYOUT_MN_MAJOR; pb.split = SPLIT_NONE;
+  if (P.split != SPLIT_NONE) {
+    pb.dst_lo = base + P.bytes_a + P.plane_b; pb.ld = P.Kp; pb.layout = LAYOUT_K_MAJOR; pb.split = P.split;
+  }
   st = cuda_status(launch_pack(pb, P.comp_double, s));
   if (st) return st;
   if (ev_mid) cudaEventRecord(ev_mid, s);
+  if (P.split != SPLIT_NONE) {
+    const void* planes[4] = {base, base + P.plane_a, base + P.bytes_a, base + P.bytes_a + P.plane_b};
+    const cudaError_t e = launch_gemm_tc(P.method, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P),
+                                         dev_err, s);
+    return e == cudaErrorNotSupported ? MXG_ENOTSUP : cuda_status(e);
+  }
   GemmArgs g;
   g.A = base; g.B = base + P.bytes_a; g.lda = P.Mp; g.ldb = P.Np; g.Kp = P.Kp;
   g.Mp = P.Mp; g.Np = P.Np; g.e = plan_epilogue(P);
@@ -446,14 +468,14 @@ int mxgemm_ex(mxg_handle h, int method, int transa, int transb, int64_t m, int64
     cudaEvent_t e0 = take_event(h), e1 = take_event(h), e2 = take_event(h);
     if (e0 && e1 && e2) {
       cudaEventRecord(e0, h->stream);
-      st = enqueue_plan(P, ws, h->stream, e1);
+      st = enqueue_plan(P, ws, h->stream, e1, h->dev_err);
       cudaEventRecord(e2, h->stream);
       h->ev_rec.push_back(e0); h->ev_rec.push_back(e1); h->ev_rec.push_back(e2);
       return st;
     }
     for (cudaEvent_t e : {e0, e1, e2}) if (e) h->ev_pool.push_back(e);
   }
-  return enqueue_plan(P, ws, h->stream, nullptr);
+  return enqueue_plan(P, ws, h->stream, nullptr, h->dev_err);
 }
 
 int mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,

@@ -1,0 +1,366 @@
+// Split-precision tensor-core contraction for computation precision single (tcgen05,
+// sm_103a): P = A' B' with each packed operand split as X = X_hi + X_lo (TF32 or
+// BF16 planes written by the pack) and
+//     P ~= A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// accumulated in FP32 in tensor memory over the whole K' (Sec. 6.3: one cast per
+// element of C), followed by the same fused epilogue as the other contractions.
+//
+// One CTA computes a 128 x 128 tile of P:
+//   warp 0      TMA producer: per k-block loads A_hi, A_lo, B_hi, B_lo tiles (128 rows
+//               x 128 bytes, 128-byte swizzle) into a 3-stage shared-memory ring;
+//   warp 1      allocates the TMEM accumulator (128 lanes x 128 FP32 columns) and one
+//               elected lane issues tcgen05.mma (M=128, N=128) for the three products;
+//               tcgen05.commit frees each stage and finally signals the epilogue;
+//   warps 2..5  epilogue: tcgen05.ld the accumulator (warp w reads TMEM lanes
+//               32*(w%4)..), pair rows or columns for complex C, alpha/beta, store.
+// Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel sets
+// the handle's error word, skips the store, waits (bounded) for its own TMA copies in
+// flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "epilogue.cuh"
+
+namespace mxg {
+
+struct TcArgs {
+  int64_t Mp, Np, Kp;   // padded real problem (multiples of 128, 128, BK)
+  EpiArgs e;
+  int* err;             // device error word set on a wait timeout (may be null)
+};
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_STAGES = 3;
+constexpr uint32_t TILE_A = TC_BM * 128;                  // bytes: 128 rows x 128 B
+constexpr uint32_t TILE_B = TC_BN * 128;
+constexpr uint32_t STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // A_hi, A_lo, B_hi, B_lo
+constexpr uint32_t TC_SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = TC_BN;
+constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on the phase of the given parity. Returns false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 0 && gtimer() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor for a K-major tile written by TMA with the 128-byte
+// swizzle: rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte
+// offset), leading byte offset unused for this layout (encoded as 1), descriptor
+// version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3fff);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+// Instruction descriptor (kind::f16 / kind::tf32): D in FP32, A and B of the given
+// format code (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  if constexpr (SPLIT == SPLIT_BF16) {
+    constexpr uint32_t idesc = make_idesc(1, TC_BM, TC_BN);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  } else {
+    constexpr uint32_t idesc = make_idesc(2, TC_BM, TC_BN);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int SPLIT, int CDT, int MODE>
+__global__ void __launch_bounds__(192, 1)
+tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
+  constexpr int ELEM = (SPLIT == SPLIT_BF16) ? 2 : 4;
+  constexpr int BK = 128 / ELEM;            // k elements per 128-byte row
+  constexpr int KSTEP = 32 / ELEM;          // k elements per MMA (16 bf16 / 8 tf32)
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;                     // 1024-aligned tiles
+  uint8_t* gen_base = smem_raw + (base - raw);
+  const uint32_t bars = base + TC_STAGES * STAGE_BYTES;             // full[S], empty[S], acc
+  uint64_t* bar_ptr = reinterpret_cast<uint64_t*>(gen_base + TC_STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 2 * TC_STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (TC_STAGES + s); };
+  const uint32_t acc_bar = bars + 8u * (2 * TC_STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * TC_BM;
+  const int64_t n0 = static_cast<int64_t>(blockIdx.y) * TC_BN;
+  const int nkb = static_cast<int>(g.Kp / BK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(acc_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
+      int issued = 0;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = static_cast<uint32_t>(kb / TC_STAGES) & 1u;
+        if (!mbar_wait(empty(s), ph ^ 1u)) { ok = false; break; }
+        if (*abort_flag) { ok = false; break; }
+        const uint32_t st = base + s * STAGE_BYTES;
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        const int32_t kx = kb * BK;
+        tma_load_2d(st, &mAh, kx, static_cast<int32_t>(m0), full(s));
+        tma_load_2d(st + TILE_A, &mAl, kx, static_cast<int32_t>(m0), full(s));
+        tma_load_2d(st + 2 * TILE_A, &mBh, kx, static_cast<int32_t>(n0), full(s));
+        tma_load_2d(st + 2 * TILE_A + TILE_B, &mBl, kx, static_cast<int32_t>(n0), full(s));
+        issued = kb + 1;
+      }
+      if (!ok) {
+        if (g.err) atomicExch(g.err, 1);
+        *abort_flag = 1;
+        // wait (bounded) for this thread's own copies still in flight
+        for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
+          mbar_wait(full(kb % TC_STAGES), static_cast<uint32_t>(kb / TC_STAGES) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        if (!mbar_wait(full(s), static_cast<uint32_t>(kb / TC_STAGES) & 1u) || *abort_flag) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * STAGE_BYTES;
+        const uint32_t a_hi = st, a_lo = st + TILE_A, b_hi = st + 2 * TILE_A, b_lo = b_hi + TILE_B;
+#pragma unroll
+        for (int kk = 0; kk < BK / KSTEP; ++kk) {
+          const uint32_t off = kk * 32;   // bytes along K inside the 128-byte row
+          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+          mma_issue<SPLIT>(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), first);
+          mma_issue<SPLIT>(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+          mma_issue<SPLIT>(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(empty(s)) : "memory");
+      }
+      if (!ok) {
+        if (g.err) atomicExch(g.err, 1);
+        *abort_flag = 1;
+      }
+      // signal the epilogue once every issued MMA has completed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(acc_bar) : "memory");
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter q = warp % 4
+    const int q = warp & 3;
+    const bool ok = mbar_wait(acc_bar, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok && g.err) atomicExch(g.err, 1);
+    const bool store = __all_sync(0xffffffffu, ok && !*abort_flag);
+    const int64_t row = m0 + 32 * q + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c0), v);
+      if (!store) continue;
+      if constexpr (MODE == OUT_ROWPAIR) {
+        // rows 2i and 2i+1 sit in lanes 2l and 2l+1: the even lane takes even
+        // columns, the odd lane odd columns
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float mine = __uint_as_float(v[j]);
+          const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+          if ((j & 1) == (lane & 1)) {
+            const float pr = (lane & 1) ? other : mine, pi = (lane & 1) ? mine : other;
+            epi_store<float, CDT, MODE>(g.e, row >> 1, n0 + c0 + j, pr, pi);
+          }
+        }
+      } else if constexpr (MODE == OUT_COLPAIR) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 2)
+          epi_store<float, CDT, MODE>(g.e, row, (n0 + c0 + j) >> 1, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          epi_store<float, CDT, MODE>(g.e, row, n0 + c0 + j, __uint_as_float(v[j]), 0.0f);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool get_encoder() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    else
+      cudaGetLastError();
+  });
+  return g_encode != nullptr;
+}
+
+// 2-D map over a K-major plane (rows x Kp elements, row pitch Kp elements), box
+// 128 rows x 128 bytes, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp) {
+  const int elem = (split == SPLIT_BF16) ? 2 : 4;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * elem};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem), 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = g_encode(map, split == SPLIT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int SPLIT, int CDT, int MODE>
+cudaError_t launch_one(const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
+  auto kern = tc_split_gemm<SPLIT, CDT, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(static_cast<unsigned>(g.Mp / TC_BM), static_cast<unsigned>(g.Np / TC_BN));
+  kern<<<grid, 192, TC_SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], g);
+  return cudaGetLastError();
+}
+
+template <int SPLIT, int CDT>
+cudaError_t launch_mode(int mode, const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
+  constexpr bool cplx = CStore<CDT>::cplx;
+  if (!cplx) {
+    if (mode != OUT_REAL) return cudaErrorInvalidValue;
+    return launch_one<SPLIT, CDT, OUT_REAL>(maps, g, s);
+  }
+  switch (mode) {
+    case OUT_RE_ONLY: return launch_one<SPLIT, CDT, (cplx ? OUT_RE_ONLY : OUT_REAL)>(maps, g, s);
+    case OUT_ROWPAIR: return launch_one<SPLIT, CDT, (cplx ? OUT_ROWPAIR : OUT_REAL)>(maps, g, s);
+    case OUT_COLPAIR: return launch_one<SPLIT, CDT, (cplx ? OUT_COLPAIR : OUT_REAL)>(maps, g, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int SPLIT>
+cudaError_t launch_split(int c_dt, int mode, const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
+  switch (c_dt) {
+    case MXG_S: return launch_mode<SPLIT, MXG_S>(mode, maps, g, s);
+    case MXG_D: return launch_mode<SPLIT, MXG_D>(mode, maps, g, s);
+    case MXG_C: return launch_mode<SPLIT, MXG_C>(mode, maps, g, s);
+    case MXG_Z: return launch_mode<SPLIT, MXG_Z>(mode, maps, g, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// planes: A_hi, A_lo (Mp x Kp, K-major), B_hi, B_lo (Np x Kp, K-major)
+cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,
+                           int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s) {
+  if (!get_encoder()) return cudaErrorNotSupported;
+  const int split = (method == MXG_METHOD_BF16X3) ? SPLIT_BF16 : SPLIT_TF32;
+  if (Mp % TC_BM || Np % TC_BN || Kp % (128 / (split == SPLIT_BF16 ? 2 : 4))) return cudaErrorInvalidValue;
+  if (Mp / TC_BM > 0x7fffffffLL || Np / TC_BN > 65535) return cudaErrorInvalidValue;
+  if (Mp == 0 || Np == 0) return cudaSuccess;
+  CUtensorMap maps[4];
+  if (!make_map(&maps[0], planes[0], split, Mp, Kp) || !make_map(&maps[1], planes[1], split, Mp, Kp) ||
+      !make_map(&maps[2], planes[2], split, Np, Kp) || !make_map(&maps[3], planes[3], split, Np, Kp))
+    return cudaErrorInvalidValue;
+  TcArgs g{Mp, Np, Kp, e, err};
+  return split == SPLIT_BF16 ? launch_split<SPLIT_BF16>(c_dt, mode, maps, g, s)
+                             : launch_split<SPLIT_TF32>(c_dt, mode, maps, g, s);
+}
+
+}  // namespace mxg

@@ -35,11 +35,13 @@ struct Plan {
   int real_products = 1;
   int64_t Mr = 0, Nr = 0, Kr = 0;   // real gemm
   int64_t Mp = 0, Np = 0, Kp = 0;   // padded to the kernel's tiles
+  int split = SPLIT_NONE;           // hi/lo planes for the tensor-core methods
+  size_t plane_a = 0, plane_b = 0;  // bytes of one plane (split methods)
   size_t bytes_a = 0, bytes_b = 0, workspace = 0;
 };
 
 int make_plan(const Call& c, int method, Plan* p);
 EpiArgs plan_epilogue(const Plan& P);
-int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid);
+int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, int* dev_err = nullptr);
 
 }  // namespace mxg

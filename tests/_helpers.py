@@ -36,8 +36,18 @@ def op(X, trans):
     return X
 
 
-def tolerance(combo, k):
-    return 4.0 * max(k, 1) * U[comp_prec(combo)] + 4.0 * U[prec_of(combo[0])]
+# Error floor of the split-precision products, relative to |a||b| per product. With
+# unit roundoff u of the plane format (BF16: 8 significant bits, u = 2^-8; TF32: 11
+# bits, u = 2^-11), X = X_hi + X_lo + r with |X - X_hi| <= u|X| and |r| <= u^2 |X|; the
+# product drops lo*lo and the two residual terms, each <= u^2 |a||b|, so the error per
+# product is <= 3 u^2 |a||b| (+ O(u^3)). By Cauchy-Schwarz the normwise error of the
+# whole product is at most that floor: 3 * 2^-16 for BF16x3, 3 * 2^-22 for TF32x3.
+U_SPLIT = {"bf16x3": 3.0 * 2.0 ** -16 * (1 + 2.0 ** -7), "tf32x3": 3.0 * 2.0 ** -22 * (1 + 2.0 ** -10)}
+
+
+def tolerance(combo, k, method=None):
+    tol = 4.0 * max(k, 1) * U[comp_prec(combo)] + 4.0 * U[prec_of(combo[0])]
+    return tol + U_SPLIT.get(method, 0.0)
 
 
 def entering_norms(combo, A, B, transa="n", transb="n"):

@@ -33,4 +33,4 @@ def run(combo, A, B, C, alpha, beta, transa="n", transb="n", method="auto"):
 
 def methods_for(combo):
     from tests._helpers import comp_prec
-    return ["ffma"] if comp_prec(combo) == "s" else ["dmma", "dfma"]
+    return ["ffma", "tf32x3", "bf16x3"] if comp_prec(combo) == "s" else ["dmma", "dfma"]

@@ -22,7 +22,7 @@ def _check(combo, A, B, C0, alpha, beta, ta="n", tb="n", method="auto", k=None):
     got = run(combo, A, B, C0, alpha, beta, ta, tb, method)
     kk = k if k is not None else (A.shape[0] if ta in "th" else A.shape[1])
     err, _ = normwise_error(combo, got, ref, A, B, C0, alpha, beta, ta, tb)
-    tol = tolerance(combo, kk)
+    tol = tolerance(combo, kk, method)
     assert err <= tol, (combo, method, ta, tb, err, tol)
     return err
 
