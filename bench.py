@@ -374,6 +374,87 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ precision workload
+PRECISION_COMBOS = ["ssss", "dsss", "cscs", "zcds", "ccss"]   # (C,A,B) sss, dss, csc, zcd, ccs + comp s
+
+
+def precision_seed(combo, n, dist):
+    return (n * 131 + PRECISION_COMBOS.index(combo) * 7 + (dist == "loguniform")) & 0x7fffffff
+
+
+def loguniform_(gen, X):
+    """Overwrite X in place with sign * 10^U(-4, 4) per real component (sign kept)."""
+    import torch
+    rv = torch.view_as_real(X) if X.is_complex() else X
+    u = torch.rand(rv.shape, generator=gen, device=rv.device, dtype=rv.dtype)
+    rv.copy_(torch.sign(rv) * torch.pow(10.0, 8.0 * u - 4.0))
+
+
+def precision_inputs(gen, combo, n, dist, dev):
+    from paper_1901_06015_gb300 import synth
+    A = synth.torch_matrix(gen, n, n, combo[1], dev)
+    B = synth.torch_matrix(gen, n, n, combo[2], dev)
+    C0 = synth.torch_matrix(gen, n, n, combo[0], dev)
+    if dist == "loguniform":
+        for X in (A, B, C0):
+            loguniform_(gen, X)
+    return A, B, C0
+
+
+def run_precision(args):
+    """Split-precision tensor-core forms vs the plain FP32 FFMA form (GFLOPS). The error
+    of every result against the FP64 oracle is checked and reported by
+    tests/test_precision_gpu.py on the same inputs."""
+    import numpy as np
+    import torch
+    import paper_1901_06015_gb300 as mx
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    h = mx.Handle(); h.set_stream(stream)
+    sizes = [int(x) for x in args.sizes.split(",")]
+    methods = ["ffma", "tf32x3", "bf16x3"]
+    results = []
+    gen = torch.Generator(device=dev)
+    for dist in ("uniform", "loguniform"):
+        for n in sizes:
+            for combo in PRECISION_COMBOS:
+                gen.manual_seed(precision_seed(combo, n, dist))
+                A, B, C0 = precision_inputs(gen, combo, n, dist, dev)
+                R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+                for meth in methods:
+                    C = C0.clone()
+                    mx.mxgemm_ex(h, meth, "n", "n", 1.0, A, B, 1.0, C, comp="s")   # warm
+                    times = []
+                    for _ in range(args.reps):
+                        C.copy_(C0)
+                        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        mx.mxgemm_ex(h, meth, "n", "n", 1.0, A, B, 1.0, C, comp="s")
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                    best = min(times)
+                    results.append({"combo": combo, "n": n, "dist": dist, "method": meth,
+                                    "gflops": round(2.0 * n ** 3 * R / best / 1e6, 1), "ms": round(best, 3)})
+                    print(json.dumps(results[-1]), file=sys.stderr, flush=True)
+                del A, B, C0, C
+                torch.cuda.empty_cache()
+    speed = {}
+    for r in results:
+        speed.setdefault(r["method"], []).append(r["gflops"])
+    gm = {m: float(np.exp(np.mean(np.log(v)))) for m, v in speed.items()}
+    line = {"metric": METRIC, "workload": "precision", "value": gm.get("bf16x3"), "unit": "GFLOPS",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32 (bf16/tf32 split planes)", "data": "synthetic",
+            "config": {"workload": "precision form: combos sss, dss, csc, zcd, ccs (comp single), m=n=k in "
+                       + args.sizes + ", uniform U[-1,1] and log-uniform sign*10^U(-4,4); best of "
+                       + str(args.reps) + " (the call includes its pack kernels)"},
+            "geomean_gflops": gm, "speedup_vs_ffma": {m: gm[m] / gm["ffma"] for m in gm},
+            "results": results}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,11 +465,16 @@ def main():
     ap.add_argument("--double-method", default="dmma", choices=["dmma", "dfma"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision"])
+    ap.add_argument("--sizes", default="4096,8192,16384")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 
