@@ -455,6 +455,83 @@ def run_precision(args):
     return 0
 
 
+# ------------------------------------------------------------------ grouped workload
+def grouped_problems(count, seed, lo, hi, dev):
+    """count independent problems: m, n, k = round(exp(U(ln lo, ln hi))), combination
+    uniform over the 128, entries U[-1, 1], alpha = 1.5, beta = -0.5."""
+    import numpy as np
+    import torch
+    from paper_1901_06015_gb300 import synth
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    combos = synth.all_combos()
+    items, flops = [], 0.0
+    for _ in range(count):
+        combo = combos[int(rng.integers(len(combos)))]
+        m, n, k = (int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi)))))) for _ in range(3))
+        A = synth.torch_matrix(gen, m, k, combo[1], dev)
+        B = synth.torch_matrix(gen, k, n, combo[2], dev)
+        C = synth.torch_matrix(gen, m, n, combo[0], dev)
+        items.append(("n", "n", 1.5, A, B, -0.5, C, combo[3]))
+        R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+        flops += 2.0 * m * n * k * R
+    return items, flops
+
+
+def run_grouped(args):
+    """One graph-captured grouped launch of 2048 problems vs 2048 separate plain calls."""
+    import torch
+    import paper_1901_06015_gb300 as mx
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    items, flops = grouped_problems(args.count, 0, 16, 1024, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = mx.Group(items, tune=True, graph=True, stream=stream)
+    create_s = time.perf_counter() - t0
+    desc = g.describe()
+    h = mx.Handle(); h.set_stream(stream)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def separate():
+        for (ta, tb, al, A, B, be, C, x) in items:
+            mx.mxgemm_ex(h, "auto", ta, tb, al, A, B, be, C, comp=x)
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms_g = timed(g.run, args.steps, args.warmup)
+    ms_s = timed(separate, args.steps, args.warmup)
+    clocks = sampler.stop()
+    # the same grouped run without the tuner (first candidate, dynamic schedule)
+    g2 = mx.Group(items, tune=False, graph=True, stream=stream)
+    ms_g2 = timed(g2.run, args.steps, args.warmup)
+    line = {"metric": METRIC, "workload": "grouped", "value": args.count / (ms_g / 1e3), "unit": "problems/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g,
+            "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"batching: {args.count} independent gemms, m,n,k = round(exp(U(ln16, ln1024))), "
+                                   "combination uniform over the 128, U[-1,1], alpha=1.5, beta=-0.5, seed 0; "
+                                   "one graph-captured grouped persistent launch (autotuned) vs separate plain calls"},
+            "grouped_gflops": flops / (ms_g / 1e3) / 1e9, "separate_ms": ms_s,
+            "separate_problems_per_s": args.count / (ms_s / 1e3), "separate_gflops": flops / (ms_s / 1e3) / 1e9,
+            "speedup_vs_separate": ms_s / ms_g, "untuned_grouped_ms": ms_g2,
+            "useful_gflop_per_step": flops / 1e9, "create_s": create_s, "group": desc, "clocks": clocks}
+    print(json.dumps(line))
+    g.close(); g2.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,7 +542,8 @@ def main():
     ap.add_argument("--double-method", default="dmma", choices=["dmma", "dfma"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision"])
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision", "grouped"])
+    ap.add_argument("--count", type=int, default=2048)
     ap.add_argument("--sizes", default="4096,8192,16384")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
@@ -475,6 +553,8 @@ def main():
         return run_reference(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "grouped":
+        return run_grouped(args)
     return run_ours(args)
 
 

@@ -176,6 +176,62 @@ int mxg_set_workspace(mxg_handle h, void* ptr, size_t bytes);
  * stream. Returns MXG_OK or MXG_ECUDA; *flag receives the word. */
 int mxg_check_device_error(mxg_handle h, int* flag);
 
+/*
+ * Grouped persistent launch: many independent gemms of uneven shapes and mixed
+ * datatype combinations in few launches. Each problem has the semantics of mxgemm
+ * (all of the rules above); problems must not write overlapping C. The paper's
+ * argument (Sec. 2.2.4) that datatype handling is orthogonal to how the loops are
+ * parallelised is what lets problems of different datatypes share one launch.
+ *
+ * mxg_group_create validates and plans every problem (the first invalid one makes it
+ * fail with that problem's status; *first_bad receives its index when first_bad is not
+ * NULL), buckets the problems by computation precision, and builds on the device:
+ * the packed operands of every problem, one pack work list per bucket and one
+ * (problem, tile) work list per bucket, ordered longest-first. A run is then one
+ * grouped pack launch and one persistent contraction launch per bucket (plus a
+ * C := beta*C launch per problem with k == 0 or alpha == 0).
+ *   method_s: MXG_METHOD_AUTO or MXG_METHOD_FFMA (single-precision bucket);
+ *   method_d: MXG_METHOD_AUTO, MXG_METHOD_DMMA or MXG_METHOD_DFMA (double bucket);
+ *   flags:    MXG_GROUP_TUNE  -- time each bucket's candidate kernels and schedules
+ *                                 (into scratch copies of C, so the problems' C are not
+ *                                 touched) and keep the fastest; decisions are cached in
+ *                                 the process by a signature of the bucket;
+ *             MXG_GROUP_GRAPH -- capture the run in a CUDA graph, replayed by each
+ *                                 mxg_group_run.
+ * The group owns its device memory (one allocation) until mxg_group_destroy, which
+ * synchronises h's stream. The problems' A, B and C pointers are read at create time
+ * and used by every run; their contents are read and written at run time.
+ */
+typedef struct {
+  int transa, transb;
+  int64_t m, n, k;
+  double alpha_re, alpha_im, beta_re, beta_im;
+  const void* A; int dtA; int64_t rsA, csA;
+  const void* B; int dtB; int64_t rsB, csB;
+  void* C; int dtC; int64_t rsC, csC;
+  int comp_prec;
+} mxg_problem;
+
+typedef struct mxg_group_s* mxg_group;
+
+enum { MXG_GROUP_TUNE = 1, MXG_GROUP_GRAPH = 2 };
+
+int mxg_group_create(mxg_handle h, int64_t count, const mxg_problem* probs, int method_s, int method_d,
+                     int flags, mxg_group* out, int64_t* first_bad);
+/* Enqueue one run of the group on its handle's stream (asynchronous). */
+int mxg_group_run(mxg_group g);
+/* Write a one-line JSON description (buckets, kernels, schedules, tiles, tuned times)
+ * into buf (NUL-terminated, truncated to len). */
+int mxg_group_describe(mxg_group g, char* buf, size_t len);
+int mxg_group_destroy(mxg_group g);
+
+/* One-shot grouped call: create (no tuning, no graph), run, synchronise, destroy. */
+int mxgemm_grouped(mxg_handle h, int64_t count, const mxg_problem* probs);
+
+/* Save / load the autotuner's decisions (text, one line per bucket signature). */
+int mxg_tune_save(const char* path);
+int mxg_tune_load(const char* path);
+
 /* Phase timing on h (tracing). When on, every call on h records CUDA events on h's
  * stream before its pack launches, between the packs and the contraction launch, and
  * after the contraction. mxg_phase_times synchronises h's stream, returns the summed

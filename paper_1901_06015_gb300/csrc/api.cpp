@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "mxg_internal.h"
+#include "context.h"
 #include "plan.h"
 #include "../../include/mxgemm.h"
 
@@ -222,38 +223,6 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
 }  // namespace mxg
 
 using namespace mxg;
-
-struct mxg_context {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool ws_owned = true;
-  int* dev_err = nullptr;
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<cudaEvent_t> ev_rec;   // triples: before packs, before contraction, after
-  std::mutex mu;
-};
-
-static cudaEvent_t take_event(mxg_context* h) {
-  if (!h->ev_pool.empty()) {
-    cudaEvent_t e = h->ev_pool.back();
-    h->ev_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return e;
-}
-
-static void recycle_events(mxg_context* h) {
-  for (cudaEvent_t e : h->ev_rec) h->ev_pool.push_back(e);
-  h->ev_rec.clear();
-}
 
 static int ensure_workspace(mxg_context* h, size_t need, void** out) {
   *out = h->ws;

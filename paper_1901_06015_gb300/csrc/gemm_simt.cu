@@ -3,143 +3,201 @@
 // over the whole K' in the computation precision (Sec. 6.3: one cast per element of
 // C, no intermediate round-off in C's precision), then alpha / beta / store.
 //
-//  * simt_gemm<float>  : FP32 FFMA, 128 x 128 CTA tile, 8 x 8 outputs per thread.
-//  * simt_gemm<double> : FP64 DFMA,  64 x 64 CTA tile, 4 x 4 outputs per thread.
-//  * dmma_gemm         : FP64 tensor-core mma.sync.m8n8k4, 64 x 64 CTA tile, 4 warps.
+//  * simt tiles (FFMA for float, DFMA for double): 256 threads as 16 x 16, tile
+//    32H x 32H x 8, each thread 2H x 2H outputs, H = elements per vector load
+//    (float: H = 4 -> 128 x 128 or H = 2 -> 64 x 64; double: H = 2 -> 64 x 64 or
+//    H = 1 -> 32 x 32).
+//  * dmma tile: FP64 tensor-core mma.sync.m8n8k4, 64 x 64 x 16, 4 warps.
 //
-// Packed operands are MN-major (element (kk, mm) at kk*ld + mm) and padded to whole
-// tiles with zeros, so the main loops have no bounds checks. Each thread owns pairs of
-// adjacent rows and adjacent columns, so the complex pairings of the 1m layouts
-// (rows 2i, 2i+1 or columns 2j, 2j+1) are formed in registers.
+// Packed operands are MN-major (element (kk, mm) at kk*ld + mm) and padded with zeros
+// (to a multiple of the tile in M/N as far as the tile grid reads, and of the k tile
+// in K), so the main loops have no bounds checks. Each output element is accumulated
+// by one thread in increasing k, so the result does not depend on the tile shape or
+// on which CTA computes the tile.
+//
+// Each kernel exists as a single-problem launch (C datatype and output mode fixed at
+// compile time) and as a grouped persistent launch that walks a device work list of
+// (problem, tile) entries from many problems, dispatching the epilogue per tile.
 #include "epilogue.cuh"
+#include "grouped.h"
 
 namespace mxg {
 namespace {
 
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using V = float4; static constexpr int n = 4; };
-template <> struct Vec16<double> { using V = double2; static constexpr int n = 2; };
+template <typename T, int H> struct VecT;
+template <> struct VecT<float, 4> { using V = float4; };
+template <> struct VecT<float, 2> { using V = float2; };
+template <> struct VecT<double, 2> { using V = double2; };
+template <> struct VecT<double, 1> { using V = double; };
 
-template <typename T>
-__device__ __forceinline__ void unpack16(const typename Vec16<T>::V& v, T* out);
-template <>
-__device__ __forceinline__ void unpack16<float>(const float4& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
-template <>
-__device__ __forceinline__ void unpack16<double>(const double2& v, double* o) { o[0] = v.x; o[1] = v.y; }
+template <typename T, int H>
+__device__ __forceinline__ void unpack(const typename VecT<T, H>::V& v, T* o) {
+  if constexpr (H == 4) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  else if constexpr (H == 2) { o[0] = v.x; o[1] = v.y; }
+  else { o[0] = v; }
+}
 
-// Generic SIMT tile: 256 threads as 16 x 16; thread (tm, tn) owns rows
-// {tm*H + i, TM/2 + tm*H + i} and columns {tn*H + j, TN/2 + tn*H + j}, i, j < H,
-// where H = 16 bytes / sizeof(T) (one vector load per half).
-template <typename T, int CDT, int MODE>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmArgs g) {
-  using V = typename Vec16<T>::V;
-  constexpr int H = Vec16<T>::n;      // elements per 16-byte vector
-  constexpr int TM = 32 * H, TN = 32 * H, TK = 8;
-  constexpr int R = 2 * H;            // outputs per thread per dimension
-  __shared__ __align__(16) T As[2][TK][TM];
-  __shared__ __align__(16) T Bs[2][TK][TN];
+template <typename T, int H>
+struct SimtSmem {
+  static constexpr int TM = 32 * H, TK = 8;
+  __align__(16) T As[2][TK][TM];
+  __align__(16) T Bs[2][TK][TM];
+};
 
+// Main loop of one 32H x 32H tile at (m0, n0); leaves the accumulators in acc.
+template <typename T, int H>
+__device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* __restrict__ B, int64_t lda,
+                                              int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
+                                              SimtSmem<T, H>& sm, T (&acc)[2 * H][2 * H]) {
+  using V = typename VecT<T, H>::V;
+  constexpr int TM = 32 * H, TK = 8, R = 2 * H;
   const int tid = threadIdx.x;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * TM;
-  const int64_t n0 = static_cast<int64_t>(blockIdx.y) * TN;
-  // global -> shared: TK rows x TM elements = 256 vectors, one per thread
   const int lrow = tid / (TM / H), lcol = (tid % (TM / H)) * H;
-  const T* Ag = static_cast<const T*>(g.A) + lrow * g.lda + m0 + lcol;
-  const T* Bg = static_cast<const T*>(g.B) + lrow * g.ldb + n0 + lcol;
+  const T* Ag = A + lrow * lda + m0 + lcol;
+  const T* Bg = B + lrow * ldb + n0 + lcol;
   V ra = __ldg(reinterpret_cast<const V*>(Ag));
   V rb = __ldg(reinterpret_cast<const V*>(Bg));
-  *reinterpret_cast<V*>(&As[0][lrow][lcol]) = ra;
-  *reinterpret_cast<V*>(&Bs[0][lrow][lcol]) = rb;
+  *reinterpret_cast<V*>(&sm.As[0][lrow][lcol]) = ra;
+  *reinterpret_cast<V*>(&sm.Bs[0][lrow][lcol]) = rb;
   __syncthreads();
-
-  T acc[R][R];
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[i][j] = T(0);
-
   const int tm = tid & 15, tn = tid >> 4;
-  const int64_t nk = g.Kp / TK;
+  const int64_t nk = Kp / TK;
   int buf = 0;
   for (int64_t kt = 0; kt < nk; ++kt) {
     const bool more = (kt + 1 < nk);
     if (more) {
-      Ag += TK * g.lda;
-      Bg += TK * g.ldb;
+      Ag += TK * lda;
+      Bg += TK * ldb;
       ra = __ldg(reinterpret_cast<const V*>(Ag));
       rb = __ldg(reinterpret_cast<const V*>(Bg));
     }
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
       T a[R], b[R];
-      unpack16<T>(*reinterpret_cast<const V*>(&As[buf][kk][tm * H]), a);
-      unpack16<T>(*reinterpret_cast<const V*>(&As[buf][kk][TM / 2 + tm * H]), a + H);
-      unpack16<T>(*reinterpret_cast<const V*>(&Bs[buf][kk][tn * H]), b);
-      unpack16<T>(*reinterpret_cast<const V*>(&Bs[buf][kk][TN / 2 + tn * H]), b + H);
+      unpack<T, H>(*reinterpret_cast<const V*>(&sm.As[buf][kk][tm * H]), a);
+      unpack<T, H>(*reinterpret_cast<const V*>(&sm.As[buf][kk][TM / 2 + tm * H]), a + H);
+      unpack<T, H>(*reinterpret_cast<const V*>(&sm.Bs[buf][kk][tn * H]), b);
+      unpack<T, H>(*reinterpret_cast<const V*>(&sm.Bs[buf][kk][TM / 2 + tn * H]), b + H);
 #pragma unroll
       for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     if (more) {
-      *reinterpret_cast<V*>(&As[buf ^ 1][lrow][lcol]) = ra;
-      *reinterpret_cast<V*>(&Bs[buf ^ 1][lrow][lcol]) = rb;
+      *reinterpret_cast<V*>(&sm.As[buf ^ 1][lrow][lcol]) = ra;
+      *reinterpret_cast<V*>(&sm.Bs[buf ^ 1][lrow][lcol]) = rb;
       __syncthreads();
       buf ^= 1;
     }
   }
+}
 
-  // Fused epilogue.
+template <typename T, int H, int CDT, int MODE>
+__device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const T (&acc)[2 * H][2 * H]) {
+  constexpr int TM = 32 * H, R = 2 * H;
+  const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
   auto row_of = [&](int i) -> int64_t { return m0 + (i < H ? tm * H + i : TM / 2 + tm * H + (i - H)); };
-  auto col_of = [&](int j) -> int64_t { return n0 + (j < H ? tn * H + j : TN / 2 + tn * H + (j - H)); };
+  auto col_of = [&](int j) -> int64_t { return n0 + (j < H ? tn * H + j : TM / 2 + tn * H + (j - H)); };
   if constexpr (MODE == OUT_ROWPAIR) {
 #pragma unroll
     for (int i = 0; i < R; i += 2)
 #pragma unroll
       for (int j = 0; j < R; ++j)
-        epi_store<T, CDT, MODE>(g.e, row_of(i) >> 1, col_of(j), acc[i][j], acc[i + 1][j]);
+        epi_store<T, CDT, MODE>(e, row_of(i) >> 1, col_of(j), acc[i][j], acc[i + 1][j]);
   } else if constexpr (MODE == OUT_COLPAIR) {
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
       for (int j = 0; j < R; j += 2)
-        epi_store<T, CDT, MODE>(g.e, row_of(i), col_of(j) >> 1, acc[i][j], acc[i][j + 1]);
+        epi_store<T, CDT, MODE>(e, row_of(i), col_of(j) >> 1, acc[i][j], acc[i][j + 1]);
   } else {
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < R; ++j)
-        epi_store<T, CDT, MODE>(g.e, row_of(i), col_of(j), acc[i][j], T(0));
+      for (int j = 0; j < R; ++j) epi_store<T, CDT, MODE>(e, row_of(i), col_of(j), acc[i][j], T(0));
   }
 }
 
-// FP64 tensor-core kernel (mma.sync.aligned.m8n8k4 .f64). 128 threads = 2 x 2 warps,
-// each warp a 32 x 32 sub-tile of 4 x 4 mma blocks. Shared rows are padded to 68
-// doubles so the fragment loads (4 k-rows x 8 m-columns per half warp) hit 16
-// distinct 8-byte banks. The accumulator tile is staged through shared memory for the
-// epilogue, which then pairs rows or columns for the complex layouts.
-constexpr int DM_T = 64, DM_TK = 16, DM_LD = DM_T + 4;
+// Runtime dispatch over the 8 valid (C datatype, output mode) pairs, once per tile.
+template <typename T, int H>
+__device__ __forceinline__ void simt_epilogue_rt(int cdt, int mode, const EpiArgs& e, int64_t m0, int64_t n0,
+                                                 const T (&acc)[2 * H][2 * H]) {
+  switch (cdt * 4 + mode) {
+    case MXG_S * 4 + OUT_REAL: simt_epilogue<T, H, MXG_S, OUT_REAL>(e, m0, n0, acc); break;
+    case MXG_D * 4 + OUT_REAL: simt_epilogue<T, H, MXG_D, OUT_REAL>(e, m0, n0, acc); break;
+    case MXG_C * 4 + OUT_RE_ONLY: simt_epilogue<T, H, MXG_C, OUT_RE_ONLY>(e, m0, n0, acc); break;
+    case MXG_C * 4 + OUT_ROWPAIR: simt_epilogue<T, H, MXG_C, OUT_ROWPAIR>(e, m0, n0, acc); break;
+    case MXG_C * 4 + OUT_COLPAIR: simt_epilogue<T, H, MXG_C, OUT_COLPAIR>(e, m0, n0, acc); break;
+    case MXG_Z * 4 + OUT_RE_ONLY: simt_epilogue<T, H, MXG_Z, OUT_RE_ONLY>(e, m0, n0, acc); break;
+    case MXG_Z * 4 + OUT_ROWPAIR: simt_epilogue<T, H, MXG_Z, OUT_ROWPAIR>(e, m0, n0, acc); break;
+    case MXG_Z * 4 + OUT_COLPAIR: simt_epilogue<T, H, MXG_Z, OUT_COLPAIR>(e, m0, n0, acc); break;
+    default: break;
+  }
+}
 
-template <int CDT, int MODE>
-__global__ void __launch_bounds__(128) dmma_gemm(GemmArgs g) {
-  __shared__ __align__(16) double smem[2 * 2 * DM_TK * DM_LD];
+template <typename T, int H, int CDT, int MODE>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmArgs g) {
+  __shared__ SimtSmem<T, H> sm;
+  T acc[2 * H][2 * H];
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 32 * H, n0 = static_cast<int64_t>(blockIdx.y) * 32 * H;
+  simt_mainloop<T, H>(static_cast<const T*>(g.A), static_cast<const T*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, sm, acc);
+  simt_epilogue<T, H, CDT, MODE>(g.e, m0, n0, acc);
+}
+
+// Fetch the next work-list index for the whole CTA (dynamic schedule: one atomic per
+// tile on the bucket's counter; static schedule: CTA b takes b, b + grid, ...).
+__device__ __forceinline__ int next_tile(int* counter, int* slot, int prev, int sched) {
+  if (sched == SCHED_STATIC) return prev < 0 ? static_cast<int>(blockIdx.x) : prev + static_cast<int>(gridDim.x);
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+  __syncthreads();
+  return *slot;
+}
+
+template <typename T, int H>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3))
+simt_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int ntiles,
+                  int* counter, int sched) {
+  __shared__ SimtSmem<T, H> sm;
+  __shared__ int slot;
+  T acc[2 * H][2 * H];
+  for (int t = next_tile(counter, &slot, -1, sched); t < ntiles; t = next_tile(counter, &slot, t, sched)) {
+    const GroupTile tl = tiles[t];
+    const GroupProb& p = probs[tl.prob];
+    const int64_t m0 = static_cast<int64_t>(tl.tm) * 32 * H, n0 = static_cast<int64_t>(tl.tn) * 32 * H;
+    __syncthreads();   // the previous tile's shared-memory reads are done
+    simt_mainloop<T, H>(static_cast<const T*>(p.A), static_cast<const T*>(p.B), p.lda, p.ldb, p.Kp, m0, n0, sm, acc);
+    simt_epilogue_rt<T, H>(p.cdt, p.mode, p.e, m0, n0, acc);
+  }
+}
+
+// ---------------------------------------------------------------- FP64 tensor core
+// 128 threads = 2 x 2 warps, each warp a 32 x 32 sub-tile of 4 x 4 mma blocks. Shared
+// rows are padded to 68 doubles so the fragment loads (4 k-rows x 8 m-columns per half
+// warp) hit 16 distinct 8-byte banks. The accumulator tile is staged through shared
+// memory for the epilogue, which then pairs rows or columns for the complex layouts.
+constexpr int DM_T = 64, DM_TK = 16, DM_LD = DM_T + 4, DM_CLD = DM_T + 1;
+constexpr int DM_SMEM = 2 * 2 * DM_TK * DM_LD;   // doubles
+static_assert(DM_T * DM_CLD <= DM_SMEM, "staging tile must fit");
+
+__device__ __forceinline__ void dmma_mainloop(const double* __restrict__ A, const double* __restrict__ B,
+                                              int64_t lda, int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
+                                              double* smem, double (&acc)[4][4][2]) {
   double* As = smem;                       // [2][TK][LD]
   double* Bs = smem + 2 * DM_TK * DM_LD;   // [2][TK][LD]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 1, wn = warp >> 1;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * DM_T;
-  const int64_t n0 = static_cast<int64_t>(blockIdx.y) * DM_T;
-  const double* A = static_cast<const double*>(g.A);
-  const double* B = static_cast<const double*>(g.B);
-
-  // global -> shared: TK x 64 doubles = 512 double2 per operand, 4 per thread.
   double2 ra[4], rb[4];
   auto gload = [&](int64_t k0) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int idx = tid + r * 128, row = idx >> 5, col = (idx & 31) * 2;
-      ra[r] = __ldg(reinterpret_cast<const double2*>(A + (k0 + row) * g.lda + m0 + col));
-      rb[r] = __ldg(reinterpret_cast<const double2*>(B + (k0 + row) * g.ldb + n0 + col));
+      ra[r] = __ldg(reinterpret_cast<const double2*>(A + (k0 + row) * lda + m0 + col));
+      rb[r] = __ldg(reinterpret_cast<const double2*>(B + (k0 + row) * ldb + n0 + col));
     }
   };
   auto sstore = [&](int buf) {
@@ -153,15 +211,12 @@ __global__ void __launch_bounds__(128) dmma_gemm(GemmArgs g) {
   gload(0);
   sstore(0);
   __syncthreads();
-
-  double acc[4][4][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-
   const int fr = lane & 3, fc = lane >> 2;
-  const int64_t nk = g.Kp / DM_TK;
+  const int64_t nk = Kp / DM_TK;
   int buf = 0;
   for (int64_t kt = 0; kt < nk; ++kt) {
     const bool more = (kt + 1 < nk);
@@ -187,37 +242,86 @@ __global__ void __launch_bounds__(128) dmma_gemm(GemmArgs g) {
       buf ^= 1;
     }
   }
+}
 
-  // Stage the 64 x 64 accumulator tile as Cs[col][row] (row contiguous).
-  constexpr int CLD = DM_T + 1;
-  static_assert(DM_T * CLD <= 2 * 2 * DM_TK * DM_LD, "staging tile must fit");
+// Stage the 64 x 64 accumulator tile as Cs[col][row] (row contiguous); ends synced.
+__device__ __forceinline__ void dmma_stage(double* smem, const double (&acc)[4][4][2]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp & 1, wn = warp >> 1, fr = lane & 3, fc = lane >> 2;
   __syncthreads();
-  double* Cs = smem;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int row = wm * 32 + i * 8 + fc;
       const int col = wn * 32 + j * 8 + fr * 2;
-      Cs[col * CLD + row] = acc[i][j][0];
-      Cs[(col + 1) * CLD + row] = acc[i][j][1];
+      smem[col * DM_CLD + row] = acc[i][j][0];
+      smem[(col + 1) * DM_CLD + row] = acc[i][j][1];
     }
   __syncthreads();
+}
+
+template <int CDT, int MODE>
+__device__ __forceinline__ void dmma_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const double* Cs) {
+  const int tid = threadIdx.x;
   if constexpr (MODE == OUT_ROWPAIR) {
     for (int idx = tid; idx < (DM_T / 2) * DM_T; idx += 128) {
       const int rp = idx % (DM_T / 2), col = idx / (DM_T / 2);
-      epi_store<double, CDT, MODE>(g.e, (m0 >> 1) + rp, n0 + col, Cs[col * CLD + 2 * rp], Cs[col * CLD + 2 * rp + 1]);
+      epi_store<double, CDT, MODE>(e, (m0 >> 1) + rp, n0 + col, Cs[col * DM_CLD + 2 * rp], Cs[col * DM_CLD + 2 * rp + 1]);
     }
   } else if constexpr (MODE == OUT_COLPAIR) {
     for (int idx = tid; idx < DM_T * (DM_T / 2); idx += 128) {
       const int row = idx % DM_T, cp = idx / DM_T;
-      epi_store<double, CDT, MODE>(g.e, m0 + row, (n0 >> 1) + cp, Cs[2 * cp * CLD + row], Cs[(2 * cp + 1) * CLD + row]);
+      epi_store<double, CDT, MODE>(e, m0 + row, (n0 >> 1) + cp, Cs[2 * cp * DM_CLD + row], Cs[(2 * cp + 1) * DM_CLD + row]);
     }
   } else {
     for (int idx = tid; idx < DM_T * DM_T; idx += 128) {
       const int row = idx % DM_T, col = idx / DM_T;
-      epi_store<double, CDT, MODE>(g.e, m0 + row, n0 + col, Cs[col * CLD + row], 0.0);
+      epi_store<double, CDT, MODE>(e, m0 + row, n0 + col, Cs[col * DM_CLD + row], 0.0);
     }
+  }
+}
+
+__device__ __forceinline__ void dmma_epilogue_rt(int cdt, int mode, const EpiArgs& e, int64_t m0, int64_t n0,
+                                                 const double* Cs) {
+  switch (cdt * 4 + mode) {
+    case MXG_S * 4 + OUT_REAL: dmma_epilogue<MXG_S, OUT_REAL>(e, m0, n0, Cs); break;
+    case MXG_D * 4 + OUT_REAL: dmma_epilogue<MXG_D, OUT_REAL>(e, m0, n0, Cs); break;
+    case MXG_C * 4 + OUT_RE_ONLY: dmma_epilogue<MXG_C, OUT_RE_ONLY>(e, m0, n0, Cs); break;
+    case MXG_C * 4 + OUT_ROWPAIR: dmma_epilogue<MXG_C, OUT_ROWPAIR>(e, m0, n0, Cs); break;
+    case MXG_C * 4 + OUT_COLPAIR: dmma_epilogue<MXG_C, OUT_COLPAIR>(e, m0, n0, Cs); break;
+    case MXG_Z * 4 + OUT_RE_ONLY: dmma_epilogue<MXG_Z, OUT_RE_ONLY>(e, m0, n0, Cs); break;
+    case MXG_Z * 4 + OUT_ROWPAIR: dmma_epilogue<MXG_Z, OUT_ROWPAIR>(e, m0, n0, Cs); break;
+    case MXG_Z * 4 + OUT_COLPAIR: dmma_epilogue<MXG_Z, OUT_COLPAIR>(e, m0, n0, Cs); break;
+    default: break;
+  }
+}
+
+template <int CDT, int MODE>
+__global__ void __launch_bounds__(128) dmma_gemm(GemmArgs g) {
+  __shared__ __align__(16) double smem[DM_SMEM];
+  double acc[4][4][2];
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * DM_T, n0 = static_cast<int64_t>(blockIdx.y) * DM_T;
+  dmma_mainloop(static_cast<const double*>(g.A), static_cast<const double*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, smem, acc);
+  dmma_stage(smem, acc);
+  dmma_epilogue<CDT, MODE>(g.e, m0, n0, smem);
+}
+
+__global__ void __launch_bounds__(128)
+dmma_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int ntiles,
+                  int* counter, int sched) {
+  __shared__ __align__(16) double smem[DM_SMEM];
+  __shared__ int slot;
+  double acc[4][4][2];
+  for (int t = next_tile(counter, &slot, -1, sched); t < ntiles; t = next_tile(counter, &slot, t, sched)) {
+    const GroupTile tl = tiles[t];
+    const GroupProb& p = probs[tl.prob];
+    const int64_t m0 = static_cast<int64_t>(tl.tm) * DM_T, n0 = static_cast<int64_t>(tl.tn) * DM_T;
+    __syncthreads();
+    dmma_mainloop(static_cast<const double*>(p.A), static_cast<const double*>(p.B), p.lda, p.ldb, p.Kp, m0, n0,
+                  smem, acc);
+    dmma_stage(smem, acc);
+    dmma_epilogue_rt(p.cdt, p.mode, p.e, m0, n0, smem);
   }
 }
 
@@ -236,13 +340,13 @@ __global__ void scale_c_kernel(EpiArgs e) {
   }
 }
 
-template <typename T, int CDT>
+template <typename T, int H, int CDT>
 cudaError_t launch_simt_mode(int mode, const GemmArgs& g, cudaStream_t s, dim3 grid) {
   switch (mode) {
-    case OUT_REAL: simt_gemm<T, CDT, OUT_REAL><<<grid, 256, 0, s>>>(g); break;
-    case OUT_RE_ONLY: simt_gemm<T, CDT, OUT_RE_ONLY><<<grid, 256, 0, s>>>(g); break;
-    case OUT_ROWPAIR: simt_gemm<T, CDT, OUT_ROWPAIR><<<grid, 256, 0, s>>>(g); break;
-    case OUT_COLPAIR: simt_gemm<T, CDT, OUT_COLPAIR><<<grid, 256, 0, s>>>(g); break;
+    case OUT_REAL: simt_gemm<T, H, CDT, OUT_REAL><<<grid, 256, 0, s>>>(g); break;
+    case OUT_RE_ONLY: simt_gemm<T, H, CDT, OUT_RE_ONLY><<<grid, 256, 0, s>>>(g); break;
+    case OUT_ROWPAIR: simt_gemm<T, H, CDT, OUT_ROWPAIR><<<grid, 256, 0, s>>>(g); break;
+    case OUT_COLPAIR: simt_gemm<T, H, CDT, OUT_COLPAIR><<<grid, 256, 0, s>>>(g); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -271,8 +375,8 @@ cudaError_t launch_for_c(int method, int mode, const GemmArgs& g, cudaStream_t s
   if (!CStore<CDT>::cplx && mode != OUT_REAL) return cudaErrorInvalidValue;
   if (CStore<CDT>::cplx && mode == OUT_REAL) return cudaErrorInvalidValue;
   switch (method) {
-    case MXG_METHOD_FFMA: return launch_simt_mode<float, CDT>(mode, g, s, grid);
-    case MXG_METHOD_DFMA: return launch_simt_mode<double, CDT>(mode, g, s, grid);
+    case MXG_METHOD_FFMA: return launch_simt_mode<float, 4, CDT>(mode, g, s, grid);
+    case MXG_METHOD_DFMA: return launch_simt_mode<double, 2, CDT>(mode, g, s, grid);
     case MXG_METHOD_DMMA: return launch_dmma_mode<CDT>(mode, g, s, grid);
   }
   return cudaErrorInvalidValue;
@@ -291,6 +395,17 @@ TileCfg tile_cfg(int method) {
   return {128, 128, 8};
 }
 
+int variant_tile(int variant) {
+  switch (variant) {
+    case VAR_FFMA_128: return 128;
+    case VAR_FFMA_64: return 64;
+    case VAR_DFMA_64: return 64;
+    case VAR_DFMA_32: return 32;
+    case VAR_DMMA_64: return 64;
+  }
+  return 0;
+}
+
 cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, cudaStream_t s) {
   switch (c_dt) {
     case MXG_S: return launch_for_c<MXG_S>(method, mode, g, s);
@@ -299,6 +414,38 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
     case MXG_Z: return launch_for_c<MXG_Z>(method, mode, g, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const GroupTile* tiles, int ntiles,
+                                int* counter, int sched, int grid, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (grid <= 0) return cudaErrorInvalidValue;
+  switch (variant) {
+    case VAR_FFMA_128: simt_gemm_grouped<float, 4><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_FFMA_64: simt_gemm_grouped<float, 2><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_DFMA_64: simt_gemm_grouped<double, 2><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_DFMA_32: simt_gemm_grouped<double, 1><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_DMMA_64: dmma_gemm_grouped<<<grid, 128, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int grouped_blocks_per_sm(int variant) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (variant) {
+    case VAR_FFMA_128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 4>, 256, 0); break;
+    case VAR_FFMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 2>, 256, 0); break;
+    case VAR_DFMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 2>, 256, 0); break;
+    case VAR_DFMA_32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 1>, 256, 0); break;
+    case VAR_DMMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dmma_gemm_grouped, 128, 0); break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
 }
 
 cudaError_t launch_scale_c(const EpiArgs& e, int c_dt, cudaStream_t s) {

@@ -1,0 +1,44 @@
+// Device work lists and launchers of the grouped persistent launch.
+#pragma once
+
+#include "mxg_internal.h"
+
+namespace mxg {
+
+// Contraction kernels a bucket of the group may run (tile size in brackets).
+enum GroupVariant : int {
+  VAR_FFMA_128 = 0,   // FP32 FFMA, 128 x 128
+  VAR_FFMA_64 = 1,    // FP32 FFMA, 64 x 64
+  VAR_DFMA_64 = 2,    // FP64 DFMA, 64 x 64
+  VAR_DFMA_32 = 3,    // reserved
+  VAR_DMMA_64 = 4     // FP64 DMMA, 64 x 64
+};
+
+// Tile schedules of the persistent kernels: DYNAMIC takes the next entry of the
+// (longest-first) work list from an atomic counter; STATIC gives CTA b the entries
+// b, b + grid, b + 2 grid, ...
+enum GroupSched : int { SCHED_DYNAMIC = 0, SCHED_STATIC = 1 };
+
+struct GroupProb {
+  const void* A;       // packed A' of the problem (MN-major)
+  const void* B;       // packed B'
+  int64_t lda, ldb;    // padded M', N'
+  int64_t Kp;          // padded K'
+  EpiArgs e;           // epilogue of the problem
+  int cdt, mode;       // C datatype, output mode
+};
+
+struct GroupTile {
+  int prob;            // index into the problem array
+  int tm, tn;          // tile coordinates in units of the variant's tile
+};
+
+int variant_tile(int variant);
+int grouped_blocks_per_sm(int variant);
+cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const GroupTile* tiles, int ntiles,
+                                int* counter, int sched, int grid, cudaStream_t s);
+int64_t pack_tiles(const PackArgs& a);
+cudaError_t launch_pack_grouped(const PackArgs* tasks, const int64_t* tile_start, int ntasks, int64_t ntiles,
+                                int comp_double, cudaStream_t s);
+
+}  // namespace mxg

@@ -27,8 +27,8 @@ namespace mxg {
 //                                           for A, Eq. (2) for B)
 enum PackPattern : int { PAT_RE = 0, PAT_SPLIT_MN = 1, PAT_SPLIT_K = 2, PAT_ONE_E = 3 };
 
-inline int pat_fk(int p) { return (p == PAT_SPLIT_K || p == PAT_ONE_E) ? 2 : 1; }
-inline int pat_fm(int p) { return (p == PAT_SPLIT_MN || p == PAT_ONE_E) ? 2 : 1; }
+__host__ __device__ inline int pat_fk(int p) { return (p == PAT_SPLIT_K || p == PAT_ONE_E) ? 2 : 1; }
+__host__ __device__ inline int pat_fm(int p) { return (p == PAT_SPLIT_MN || p == PAT_ONE_E) ? 2 : 1; }
 
 // How the real product P (M' x N') maps onto C.
 //   OUT_REAL    C real: C(i,j) <- P(i,j)                  (cases 0, 1a, 1b, 2ab)

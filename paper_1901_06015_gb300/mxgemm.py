@@ -28,6 +28,15 @@ class PlanInfo(ctypes.Structure):
                 ("real_products", _i32), ("flops", _dbl), ("workspace_bytes", _sz)]
 
 
+class Problem(ctypes.Structure):
+    """mxg_problem of include/mxgemm.h."""
+    _fields_ = [("transa", _i32), ("transb", _i32), ("m", _i64), ("n", _i64), ("k", _i64),
+                ("alpha_re", _dbl), ("alpha_im", _dbl), ("beta_re", _dbl), ("beta_im", _dbl),
+                ("A", _vp), ("dtA", _i32), ("rsA", _i64), ("csA", _i64),
+                ("B", _vp), ("dtB", _i32), ("rsB", _i64), ("csB", _i64),
+                ("C", _vp), ("dtC", _i32), ("rsC", _i64), ("csC", _i64), ("comp_prec", _i32)]
+
+
 class MxgError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = status
@@ -67,6 +76,21 @@ def lib():
             L.mxg_check_device_error.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.mxgemm_noalloc.restype = _i32
             L.mxgemm_noalloc.argtypes = [_vp, _i32] + _GEMM_TAIL
+            L.mxg_group_create.restype = _i32
+            L.mxg_group_create.argtypes = [_vp, _i64, ctypes.POINTER(Problem), _i32, _i32, _i32,
+                                           ctypes.POINTER(_vp), ctypes.POINTER(_i64)]
+            L.mxg_group_run.restype = _i32
+            L.mxg_group_run.argtypes = [_vp]
+            L.mxg_group_describe.restype = _i32
+            L.mxg_group_describe.argtypes = [_vp, ctypes.c_char_p, _sz]
+            L.mxg_group_destroy.restype = _i32
+            L.mxg_group_destroy.argtypes = [_vp]
+            L.mxgemm_grouped.restype = _i32
+            L.mxgemm_grouped.argtypes = [_vp, _i64, ctypes.POINTER(Problem)]
+            L.mxg_tune_save.restype = _i32
+            L.mxg_tune_save.argtypes = [ctypes.c_char_p]
+            L.mxg_tune_load.restype = _i32
+            L.mxg_tune_load.argtypes = [ctypes.c_char_p]
             L.mxg_set_phase_timing.restype = _i32
             L.mxg_set_phase_timing.argtypes = [_vp, _i32]
             L.mxg_phase_times.restype = _i32
@@ -230,6 +254,85 @@ def mxgemm_noalloc(method, transa, transb, alpha, A, B, beta, C, comp="c", strea
     if st:
         raise MxgError(st, "mxgemm_noalloc")
     return C
+
+
+def make_problems(items):
+    """items: iterable of (transa, transb, alpha, A, B, beta, C, comp) on torch tensors.
+    Returns a ctypes array of mxg_problem."""
+    items = list(items)
+    arr = (Problem * max(len(items), 1))()
+    for i, (ta, tb, alpha, A, B, beta, C, comp) in enumerate(items):
+        v = _args(ta, tb, alpha, A, B, beta, C, comp)
+        p = arr[i]
+        (p.transa, p.transb, p.m, p.n, p.k, p.alpha_re, p.alpha_im, p.A, p.dtA, p.rsA, p.csA,
+         p.B, p.dtB, p.rsB, p.csB, p.beta_re, p.beta_im, p.C, p.dtC, p.rsC, p.csC, p.comp_prec) = \
+            (v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7].value or 0, v[8], v[9], v[10],
+             v[11].value or 0, v[12], v[13], v[14], v[15], v[16], v[17].value or 0, v[18], v[19], v[20], v[21])
+    return arr, len(items)
+
+
+class Group:
+    """An mxg_group: a grouped persistent launch over many problems (see
+    mxg_group_create). ``tune``: autotune kernels and schedules per bucket; ``graph``:
+    capture the run in a CUDA graph."""
+
+    def __init__(self, items, handle=None, method_s="auto", method_d="auto", tune=True, graph=True, stream=None):
+        import torch
+        if handle is None:
+            handle = Handle()
+            handle.set_stream(stream if stream is not None else torch.cuda.current_stream())
+        self.handle = handle
+        self._arr, n = make_problems(items)
+        g = ctypes.c_void_p()
+        bad = _i64(-1)
+        flags = (1 if tune else 0) | (2 if graph else 0)
+        st = lib().mxg_group_create(handle.h, n, self._arr, METHODS[method_s], METHODS[method_d], flags,
+                                    ctypes.byref(g), ctypes.byref(bad))
+        if st:
+            raise MxgError(st, f"mxg_group_create (problem {bad.value})")
+        self.g = g
+
+    def run(self):
+        st = lib().mxg_group_run(self.g)
+        if st:
+            raise MxgError(st, "mxg_group_run")
+
+    def describe(self):
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        lib().mxg_group_describe(self.g, buf, 8192)
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "g", None):
+            lib().mxg_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mxgemm_grouped(items, handle=None, stream=None):
+    """One-shot grouped call (no tuning, no graph); synchronises the stream."""
+    import torch
+    if handle is None:
+        handle = _handle_for_current()
+        handle.set_stream(stream if stream is not None else torch.cuda.current_stream())
+    arr, n = make_problems(items)
+    st = lib().mxgemm_grouped(handle.h, n, arr)
+    if st:
+        raise MxgError(st, "mxgemm_grouped")
+
+
+def mxg_tune_save(path):
+    return lib().mxg_tune_save(path.encode())
+
+
+def mxg_tune_load(path):
+    return lib().mxg_tune_load(path.encode())
 
 
 def mxg_plan(combo_or_dts, m, n, k, transa="n", transb="n", alpha=1.0, method="auto",

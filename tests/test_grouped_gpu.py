@@ -1,0 +1,140 @@
+"""Grouped persistent launch (GPU): many problems of mixed datatype combinations and
+uneven shapes in one grouped pack launch + one persistent contraction launch per
+computation precision, optionally autotuned and captured in a CUDA graph. Each result
+must equal the same problem run alone (bit for bit, same method family) and the oracle
+within tolerance."""
+import numpy as np
+import pytest
+
+from oracle import oracle_mxgemm
+from paper_1901_06015_gb300 import synth
+from tests._helpers import normwise_error, tolerance
+from tests.gpu_util import to_device
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _problems(seed, count, lo=1, hi=300, trans=True):
+    rng = np.random.default_rng(seed)
+    combos = synth.all_combos()
+    out = []
+    for i in range(count):
+        combo = combos[int(rng.integers(len(combos)))]
+        m, n, k = (int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for _ in range(3))
+        ta = "ntch"[int(rng.integers(4))] if trans else "n"
+        tb = "ntch"[int(rng.integers(4))] if trans else "n"
+        A, B, C = synth.problem(int(rng.integers(1 << 30)), combo, m, n, k, transa=ta, transb=tb,
+                                order_c="FC"[int(rng.integers(2))])
+        alpha = complex(1.25, -0.5) if all(c in "cz" for c in combo[:3]) else 1.5
+        out.append(dict(combo=combo, ta=ta, tb=tb, alpha=alpha, beta=-0.5, A=A, B=B, C=C))
+    return out
+
+
+def _device_items(probs):
+    items, dev = [], []
+    for p in probs:
+        dA, dB, dC = to_device(p["A"]), to_device(p["B"]), to_device(p["C"])
+        dev.append((dA, dB, dC))
+        items.append((p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, p["combo"][3]))
+    return items, dev
+
+
+def _solo(p, method_s="ffma", method_d="dmma"):
+    import paper_1901_06015_gb300 as mx
+    dA, dB, dC = to_device(p["A"]), to_device(p["B"]), to_device(p["C"])
+    from tests._helpers import comp_prec
+    meth = method_s if comp_prec(p["combo"]) == "s" else method_d
+    mx.mxgemm_ex(None, meth, p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, comp=p["combo"][3])
+    torch.cuda.synchronize()
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("tune,graph", [(False, False), (True, True)])
+def test_grouped_equals_solo_and_oracle(tune, graph):
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(1, 96)
+    items, dev = _device_items(probs)
+    g = mx.Group(items, method_d="dmma", tune=tune, graph=graph)
+    g.run()
+    torch.cuda.synchronize()
+    desc = g.describe()
+    assert desc["graph"] == graph
+    for p, (_, _, dC) in zip(probs, dev):
+        got = dC.cpu().numpy()
+        assert np.array_equal(got, _solo(p)), p["combo"]
+        ref_C = np.array(p["C"], order="K")
+        ref = oracle_mxgemm(p["ta"], p["tb"], p["alpha"], p["A"], p["B"], p["beta"], ref_C, comp=p["combo"][3])
+        k = p["A"].shape[0] if p["ta"] in "th" else p["A"].shape[1]
+        err, _ = normwise_error(p["combo"], got, ref, p["A"], p["B"], p["C"], p["alpha"], p["beta"], p["ta"], p["tb"])
+        assert err <= tolerance(p["combo"], k), (p["combo"], err)
+    g.close()
+
+
+def test_grouped_auto_double_kernel_within_tolerance_and_replay():
+    """method_d = auto lets the tuner pick DMMA or DFMA; two graph replays equal two
+    solo applications (beta != 0, so each run changes C)."""
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(2, 64, trans=False)
+    items, dev = _device_items(probs)
+    g = mx.Group(items, tune=True, graph=True)
+    g.run()
+    g.run()
+    torch.cuda.synchronize()
+    for p, (_, _, dC) in zip(probs, dev):
+        once = dict(p)
+        ref_C = np.array(p["C"], order="K")
+        oracle_mxgemm("n", "n", p["alpha"], p["A"], p["B"], p["beta"], ref_C, comp=p["combo"][3])
+        C1 = ref_C.copy()
+        ref2 = oracle_mxgemm("n", "n", p["alpha"], p["A"], p["B"], p["beta"], ref_C, comp=p["combo"][3])
+        got = dC.cpu().numpy()
+        err, _ = normwise_error(p["combo"], got, ref2, p["A"], p["B"], C1, p["alpha"], p["beta"])
+        assert err <= 2 * tolerance(p["combo"], p["A"].shape[1]), (p["combo"], err)
+    g.close()
+
+
+def test_grouped_scale_and_noop_problems():
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(3, 8, trans=False)
+    # k == 0 (scale only) and m == 0 (nothing) entries
+    A0 = np.zeros((5, 0), dtype=np.complex128); B0 = np.zeros((0, 4), dtype=np.float32)
+    C0 = synth.matrix(np.random.default_rng(0), 5, 4, "z")
+    probs.append(dict(combo="zdsd", ta="n", tb="n", alpha=1.0, beta=-0.5, A=A0, B=B0, C=C0))
+    items, dev = _device_items(probs)
+    Cm = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    items.append(("n", "n", 1.0, torch.zeros((0, 2), dtype=torch.float64, device="cuda"),
+                  torch.zeros((2, 3), dtype=torch.float64, device="cuda"), 1.0, Cm, "d"))
+    g = mx.Group(items, tune=False, graph=True)
+    g.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(dev[-1][2].cpu().numpy(), (-0.5 * C0).astype(C0.dtype))
+    for p, (_, _, dC) in list(zip(probs, dev))[:-1]:
+        assert np.array_equal(dC.cpu().numpy(), _solo(p))
+    g.close()
+
+
+def test_grouped_reports_first_invalid_problem():
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(4, 5, trans=False)
+    items, _ = _device_items(probs)
+    # problem 3: case 1b (C, A real; B complex) with a complex alpha -> status 2
+    A = torch.zeros((4, 3), dtype=torch.float32, device="cuda").t().contiguous().t()
+    B = torch.zeros((3, 2), dtype=torch.complex64, device="cuda").t().contiguous().t()
+    C = torch.zeros((4, 2), dtype=torch.float32, device="cuda").t().contiguous().t()
+    items[3] = ("n", "n", 1.0 + 1.0j, A, B, 0.0, C, "s")
+    with pytest.raises(mx.MxgError) as e:
+        mx.Group(items, tune=False, graph=False)
+    assert e.value.status == 2 and "problem 3" in str(e.value)
+
+
+def test_one_shot_grouped_call():
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(5, 16, trans=False)
+    items, dev = _device_items(probs)
+    mx.mxgemm_grouped(items)
+    torch.cuda.synchronize()
+    for p, (_, _, dC) in zip(probs, dev):
+        ref_C = np.array(p["C"], order="K")
+        ref = oracle_mxgemm("n", "n", p["alpha"], p["A"], p["B"], p["beta"], ref_C, comp=p["combo"][3])
+        err, _ = normwise_error(p["combo"], dC.cpu().numpy(), ref, p["A"], p["B"], p["C"], p["alpha"], p["beta"])
+        assert err <= tolerance(p["combo"], p["A"].shape[1])
