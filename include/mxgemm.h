@@ -232,6 +232,55 @@ int mxgemm_grouped(mxg_handle h, int64_t count, const mxg_problem* probs);
 int mxg_tune_save(const char* path);
 int mxg_tune_load(const char* path);
 
+/*
+ * Serving loop: a request server with continuous batching. Requests (each an
+ * mxg_problem with the semantics of mxgemm, device operands owned by the caller) are
+ * submitted from any host thread at any time. A worker thread admits them by HBM
+ * footprint -- bytes of A, B, C plus the packed operands -- while the footprint of the
+ * requests in flight stays within hbm_budget_bytes; their packed operands are carved
+ * from one device arena of that size (first-fit free list with coalescing) and stay
+ * resident until the request completes. Admitted work is spread over n_streams
+ * streams and overlaps on the device: requests of at most small_flops useful flops go
+ * to a high-priority stream, larger ones round-robin over the others (flag
+ * MXG_SERVE_FIFO instead sends every request to stream 0 in submission order, with no
+ * priority, which is the serial baseline). When the head of the queue does not fit,
+ * later small requests that fit are admitted past it. Completion is observed with one
+ * CUDA event per request; times are seconds on the server's clock (mxg_server_now):
+ * arrival = when submitted, admit = when enqueued, done = when the request's last
+ * kernel finished on the device.
+ */
+typedef struct mxg_server_s* mxg_server;
+
+typedef struct {
+  uint64_t id;        /* as returned by mxg_server_submit */
+  int status;         /* MXG_OK or the error of planning / launching */
+  int stream;         /* stream index the request ran on (-1 if it never ran) */
+  double arrival, admit, done;
+  double flops;       /* useful flops 2mnk R */
+  size_t footprint;   /* bytes counted against the budget */
+} mxg_completion;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, failed;
+  size_t bytes_in_flight, peak_bytes_in_flight, budget;
+  int64_t max_in_flight, queue_len;
+} mxg_server_stats;
+
+enum { MXG_SERVE_FIFO = 1 };
+
+int mxg_server_create(int n_streams, size_t hbm_budget_bytes, double small_flops, int method_s, int method_d,
+                      int flags, mxg_server* out);
+/* Thread-safe; never blocks on the device. *id receives the request id. */
+int mxg_server_submit(mxg_server s, const mxg_problem* p, uint64_t* id);
+/* Move up to max completions into out (*n receives the count); never blocks. */
+int mxg_server_poll(mxg_server s, mxg_completion* out, int max, int* n);
+/* Block until every submitted request has completed (or timeout_s passes: MXG_ETIMEOUT). */
+int mxg_server_drain(mxg_server s, double timeout_s);
+int mxg_server_get_stats(mxg_server s, mxg_server_stats* st);
+double mxg_server_now(mxg_server s);
+/* Drains, stops the worker, frees the arena and streams. */
+int mxg_server_destroy(mxg_server s);
+
 /* Phase timing on h (tracing). When on, every call on h records CUDA events on h's
  * stream before its pack launches, between the packs and the contraction launch, and
  * after the contraction. mxg_phase_times synchronises h's stream, returns the summed

@@ -37,6 +37,18 @@ class Problem(ctypes.Structure):
                 ("C", _vp), ("dtC", _i32), ("rsC", _i64), ("csC", _i64), ("comp_prec", _i32)]
 
 
+class Completion(ctypes.Structure):
+    """mxg_completion of include/mxgemm.h."""
+    _fields_ = [("id", ctypes.c_uint64), ("status", _i32), ("stream", _i32), ("arrival", _dbl),
+                ("admit", _dbl), ("done", _dbl), ("flops", _dbl), ("footprint", _sz)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("bytes_in_flight", _sz), ("peak_bytes_in_flight", _sz),
+                ("budget", _sz), ("max_in_flight", _i64), ("queue_len", _i64)]
+
+
 class MxgError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = status
@@ -91,6 +103,20 @@ def lib():
             L.mxg_tune_save.argtypes = [ctypes.c_char_p]
             L.mxg_tune_load.restype = _i32
             L.mxg_tune_load.argtypes = [ctypes.c_char_p]
+            L.mxg_server_create.restype = _i32
+            L.mxg_server_create.argtypes = [_i32, _sz, _dbl, _i32, _i32, _i32, ctypes.POINTER(_vp)]
+            L.mxg_server_submit.restype = _i32
+            L.mxg_server_submit.argtypes = [_vp, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_uint64)]
+            L.mxg_server_poll.restype = _i32
+            L.mxg_server_poll.argtypes = [_vp, ctypes.POINTER(Completion), _i32, ctypes.POINTER(_i32)]
+            L.mxg_server_drain.restype = _i32
+            L.mxg_server_drain.argtypes = [_vp, _dbl]
+            L.mxg_server_get_stats.restype = _i32
+            L.mxg_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+            L.mxg_server_now.restype = _dbl
+            L.mxg_server_now.argtypes = [_vp]
+            L.mxg_server_destroy.restype = _i32
+            L.mxg_server_destroy.argtypes = [_vp]
             L.mxg_set_phase_timing.restype = _i32
             L.mxg_set_phase_timing.argtypes = [_vp, _i32]
             L.mxg_phase_times.restype = _i32
@@ -307,6 +333,69 @@ class Group:
         if getattr(self, "g", None):
             lib().mxg_group_destroy(self.g)
             self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """An mxg_server: continuous-batching request server (see mxg_server_create).
+    ``fifo=True`` gives the serial baseline (one stream, submission order)."""
+
+    def __init__(self, n_streams=4, hbm_budget_bytes=16 << 30, small_flops=5e7, method_s="auto",
+                 method_d="auto", fifo=False):
+        s = ctypes.c_void_p()
+        st = lib().mxg_server_create(int(n_streams), int(hbm_budget_bytes), float(small_flops), METHODS[method_s],
+                                     METHODS[method_d], 1 if fifo else 0, ctypes.byref(s))
+        if st:
+            raise MxgError(st, "mxg_server_create")
+        self.s = s
+        self._keep = {}
+
+    def submit(self, item, keep=None):
+        """item: (transa, transb, alpha, A, B, beta, C, comp) on device tensors. ``keep``
+        (optional) is held until the request completes (e.g. the tensors)."""
+        arr, _ = make_problems([item])
+        rid = ctypes.c_uint64(0)
+        st = lib().mxg_server_submit(self.s, arr, ctypes.byref(rid))
+        if st:
+            raise MxgError(st, "mxg_server_submit")
+        if keep is not None:
+            self._keep[rid.value] = keep
+        return rid.value
+
+    def poll(self, max_items=4096):
+        buf = (Completion * max_items)()
+        n = _i32(0)
+        lib().mxg_server_poll(self.s, buf, max_items, ctypes.byref(n))
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._keep.pop(c.id, None)
+            out.append({"id": c.id, "status": c.status, "stream": c.stream, "arrival": c.arrival,
+                        "admit": c.admit, "done": c.done, "flops": c.flops, "footprint": c.footprint})
+        return out
+
+    def drain(self, timeout_s=600.0):
+        st = lib().mxg_server_drain(self.s, float(timeout_s))
+        if st:
+            raise MxgError(st, "mxg_server_drain")
+
+    def stats(self):
+        st = ServerStats()
+        lib().mxg_server_get_stats(self.s, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def now(self):
+        return lib().mxg_server_now(self.s)
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().mxg_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:
