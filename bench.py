@@ -106,24 +106,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
-    for f in ("gemm_simt.cu", "epilogue.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1901_06015_gb300", "csrc", f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_per_launch(kernel):
-    """dram bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json), if
+    the counters were taken on the kernel's current source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p)).get(kernel)
+        if not d or d.get("source_hash") != kernel_source_hash(d["source_files"]):
+            return None
     except Exception:
-        return None
-    if not d or d.get("source_hash") != kernel_source_hash():
         return None
     return d.get("dram_bytes_per_launch_at_bench_size")
 
@@ -628,6 +628,44 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ single-call workload
+def run_single(args):
+    """Repeated calls of one combination with one method (micro-benchmark, and the
+    small case the ncu captures run)."""
+    import torch
+    import paper_1901_06015_gb300 as mx
+    from paper_1901_06015_gb300 import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    combo, n = args.combo, args.size
+    gen = torch.Generator(device=dev); gen.manual_seed(3)
+    A = synth.torch_matrix(gen, n, n, combo[1], dev)
+    B = synth.torch_matrix(gen, n, n, combo[2], dev)
+    C = synth.torch_matrix(gen, n, n, combo[0], dev)
+    h = mx.Handle(); h.set_stream(stream)
+    R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+    times = []
+    h.set_phase_timing(True)
+    for i in range(args.warmup + args.reps):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mx.mxgemm_ex(h, args.method, "n", "n", 1.0, A, B, 1.0, C, comp=combo[3])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i == args.warmup - 1 or (args.warmup == 0 and i == 0):
+            h.phase_times()
+        if i >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    pack_ms, con_ms, nl = h.phase_times()
+    fl = 2.0 * n ** 3 * R
+    line = {"workload": "single", "combo": combo, "method": args.method, "n": n, "reps": args.reps,
+            "best_ms": min(times), "gflops": fl / min(times) / 1e6,
+            "contraction_ms_mean": con_ms / max(nl, 1), "pack_ms_mean": pack_ms / max(nl, 1),
+            "contraction_tflops": fl / (con_ms / max(nl, 1)) / 1e9 if nl else None}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -638,8 +676,10 @@ def main():
     ap.add_argument("--double-method", default="dmma", choices=["dmma", "dfma"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision", "grouped", "serving"])
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision", "grouped", "serving", "single"])
     ap.add_argument("--count", type=int, default=2048)
+    ap.add_argument("--combo", default="dddd")
+    ap.add_argument("--method", default="auto")
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--streams", type=int, default=4)
@@ -659,6 +699,8 @@ def main():
         return run_grouped(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "single":
+        return run_single(args)
     return run_ours(args)
 
 

@@ -5,9 +5,9 @@
 //
 //  * simt tiles (FFMA for float, DFMA for double): 256 threads as 16 x 16, tile
 //    32H x 32H x 8, each thread 2H x 2H outputs, H = elements per vector load
-//    (float: H = 4 -> 128 x 128 or H = 2 -> 64 x 64; double: H = 2 -> 64 x 64 or
-//    H = 1 -> 32 x 32).
-//  * dmma tile: FP64 tensor-core mma.sync.m8n8k4, 64 x 64 x 16, 4 warps.
+//    (float: H = 4 -> 128 x 128 or H = 2 -> 64 x 64; double: H = 2 -> 64 x 64).
+//    H must be even: the complex epilogue pairs a thread's rows 2i, 2i+1 (or columns).
+//  (The FP64 tensor-core kernel is in gemm_dmma.cu.)
 //
 // Packed operands are MN-major (element (kk, mm) at kk*ld + mm) and padded with zeros
 // (to a multiple of the tile in M/N as far as the tile grid reads, and of the k tile
@@ -28,7 +28,6 @@ template <typename T, int H> struct VecT;
 template <> struct VecT<float, 4> { using V = float4; };
 template <> struct VecT<float, 2> { using V = float2; };
 template <> struct VecT<double, 2> { using V = double2; };
-template <> struct VecT<double, 1> { using V = double; };
 
 template <typename T, int H>
 __device__ __forceinline__ void unpack(const typename VecT<T, H>::V& v, T* o) {
@@ -148,16 +147,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmA
   simt_epilogue<T, H, CDT, MODE>(g.e, m0, n0, acc);
 }
 
-// Fetch the next work-list index for the whole CTA (dynamic schedule: one atomic per
-// tile on the bucket's counter; static schedule: CTA b takes b, b + grid, ...).
-__device__ __forceinline__ int next_tile(int* counter, int* slot, int prev, int sched) {
-  if (sched == SCHED_STATIC) return prev < 0 ? static_cast<int>(blockIdx.x) : prev + static_cast<int>(gridDim.x);
-  __syncthreads();
-  if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
-  __syncthreads();
-  return *slot;
-}
-
 template <typename T, int H>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3))
 simt_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int ntiles,
@@ -172,156 +161,6 @@ simt_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restri
     __syncthreads();   // the previous tile's shared-memory reads are done
     simt_mainloop<T, H>(static_cast<const T*>(p.A), static_cast<const T*>(p.B), p.lda, p.ldb, p.Kp, m0, n0, sm, acc);
     simt_epilogue_rt<T, H>(p.cdt, p.mode, p.e, m0, n0, acc);
-  }
-}
-
-// ---------------------------------------------------------------- FP64 tensor core
-// 128 threads = 2 x 2 warps, each warp a 32 x 32 sub-tile of 4 x 4 mma blocks. Shared
-// rows are padded to 68 doubles so the fragment loads (4 k-rows x 8 m-columns per half
-// warp) hit 16 distinct 8-byte banks. The accumulator tile is staged through shared
-// memory for the epilogue, which then pairs rows or columns for the complex layouts.
-constexpr int DM_T = 64, DM_TK = 16, DM_LD = DM_T + 4, DM_CLD = DM_T + 1;
-constexpr int DM_SMEM = 2 * 2 * DM_TK * DM_LD;   // doubles
-static_assert(DM_T * DM_CLD <= DM_SMEM, "staging tile must fit");
-
-__device__ __forceinline__ void dmma_mainloop(const double* __restrict__ A, const double* __restrict__ B,
-                                              int64_t lda, int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
-                                              double* smem, double (&acc)[4][4][2]) {
-  double* As = smem;                       // [2][TK][LD]
-  double* Bs = smem + 2 * DM_TK * DM_LD;   // [2][TK][LD]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 1, wn = warp >> 1;
-  double2 ra[4], rb[4];
-  auto gload = [&](int64_t k0) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int idx = tid + r * 128, row = idx >> 5, col = (idx & 31) * 2;
-      ra[r] = __ldg(reinterpret_cast<const double2*>(A + (k0 + row) * lda + m0 + col));
-      rb[r] = __ldg(reinterpret_cast<const double2*>(B + (k0 + row) * ldb + n0 + col));
-    }
-  };
-  auto sstore = [&](int buf) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int idx = tid + r * 128, row = idx >> 5, col = (idx & 31) * 2;
-      *reinterpret_cast<double2*>(&As[(buf * DM_TK + row) * DM_LD + col]) = ra[r];
-      *reinterpret_cast<double2*>(&Bs[(buf * DM_TK + row) * DM_LD + col]) = rb[r];
-    }
-  };
-  gload(0);
-  sstore(0);
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-  const int fr = lane & 3, fc = lane >> 2;
-  const int64_t nk = Kp / DM_TK;
-  int buf = 0;
-  for (int64_t kt = 0; kt < nk; ++kt) {
-    const bool more = (kt + 1 < nk);
-    if (more) gload((kt + 1) * DM_TK);
-#pragma unroll
-    for (int kk = 0; kk < DM_TK; kk += 4) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[(buf * DM_TK + kk + fr) * DM_LD + wm * 32 + i * 8 + fc];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[(buf * DM_TK + kk + fr) * DM_LD + wn * 32 + j * 8 + fc];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
-                       : "+d"(acc[i][j][0]), "+d"(acc[i][j][1])
-                       : "d"(a[i]), "d"(b[j]));
-    }
-    if (more) {
-      sstore(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
-    }
-  }
-}
-
-// Stage the 64 x 64 accumulator tile as Cs[col][row] (row contiguous); ends synced.
-__device__ __forceinline__ void dmma_stage(double* smem, const double (&acc)[4][4][2]) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 1, wn = warp >> 1, fr = lane & 3, fc = lane >> 2;
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int row = wm * 32 + i * 8 + fc;
-      const int col = wn * 32 + j * 8 + fr * 2;
-      smem[col * DM_CLD + row] = acc[i][j][0];
-      smem[(col + 1) * DM_CLD + row] = acc[i][j][1];
-    }
-  __syncthreads();
-}
-
-template <int CDT, int MODE>
-__device__ __forceinline__ void dmma_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const double* Cs) {
-  const int tid = threadIdx.x;
-  if constexpr (MODE == OUT_ROWPAIR) {
-    for (int idx = tid; idx < (DM_T / 2) * DM_T; idx += 128) {
-      const int rp = idx % (DM_T / 2), col = idx / (DM_T / 2);
-      epi_store<double, CDT, MODE>(e, (m0 >> 1) + rp, n0 + col, Cs[col * DM_CLD + 2 * rp], Cs[col * DM_CLD + 2 * rp + 1]);
-    }
-  } else if constexpr (MODE == OUT_COLPAIR) {
-    for (int idx = tid; idx < DM_T * (DM_T / 2); idx += 128) {
-      const int row = idx % DM_T, cp = idx / DM_T;
-      epi_store<double, CDT, MODE>(e, m0 + row, (n0 >> 1) + cp, Cs[2 * cp * DM_CLD + row], Cs[(2 * cp + 1) * DM_CLD + row]);
-    }
-  } else {
-    for (int idx = tid; idx < DM_T * DM_T; idx += 128) {
-      const int row = idx % DM_T, col = idx / DM_T;
-      epi_store<double, CDT, MODE>(e, m0 + row, n0 + col, Cs[col * DM_CLD + row], 0.0);
-    }
-  }
-}
-
-__device__ __forceinline__ void dmma_epilogue_rt(int cdt, int mode, const EpiArgs& e, int64_t m0, int64_t n0,
-                                                 const double* Cs) {
-  switch (cdt * 4 + mode) {
-    case MXG_S * 4 + OUT_REAL: dmma_epilogue<MXG_S, OUT_REAL>(e, m0, n0, Cs); break;
-    case MXG_D * 4 + OUT_REAL: dmma_epilogue<MXG_D, OUT_REAL>(e, m0, n0, Cs); break;
-    case MXG_C * 4 + OUT_RE_ONLY: dmma_epilogue<MXG_C, OUT_RE_ONLY>(e, m0, n0, Cs); break;
-    case MXG_C * 4 + OUT_ROWPAIR: dmma_epilogue<MXG_C, OUT_ROWPAIR>(e, m0, n0, Cs); break;
-    case MXG_C * 4 + OUT_COLPAIR: dmma_epilogue<MXG_C, OUT_COLPAIR>(e, m0, n0, Cs); break;
-    case MXG_Z * 4 + OUT_RE_ONLY: dmma_epilogue<MXG_Z, OUT_RE_ONLY>(e, m0, n0, Cs); break;
-    case MXG_Z * 4 + OUT_ROWPAIR: dmma_epilogue<MXG_Z, OUT_ROWPAIR>(e, m0, n0, Cs); break;
-    case MXG_Z * 4 + OUT_COLPAIR: dmma_epilogue<MXG_Z, OUT_COLPAIR>(e, m0, n0, Cs); break;
-    default: break;
-  }
-}
-
-template <int CDT, int MODE>
-__global__ void __launch_bounds__(128) dmma_gemm(GemmArgs g) {
-  __shared__ __align__(16) double smem[DM_SMEM];
-  double acc[4][4][2];
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * DM_T, n0 = static_cast<int64_t>(blockIdx.y) * DM_T;
-  dmma_mainloop(static_cast<const double*>(g.A), static_cast<const double*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, smem, acc);
-  dmma_stage(smem, acc);
-  dmma_epilogue<CDT, MODE>(g.e, m0, n0, smem);
-}
-
-__global__ void __launch_bounds__(128)
-dmma_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int ntiles,
-                  int* counter, int sched) {
-  __shared__ __align__(16) double smem[DM_SMEM];
-  __shared__ int slot;
-  double acc[4][4][2];
-  for (int t = next_tile(counter, &slot, -1, sched); t < ntiles; t = next_tile(counter, &slot, t, sched)) {
-    const GroupTile tl = tiles[t];
-    const GroupProb& p = probs[tl.prob];
-    const int64_t m0 = static_cast<int64_t>(tl.tm) * DM_T, n0 = static_cast<int64_t>(tl.tn) * DM_T;
-    __syncthreads();
-    dmma_mainloop(static_cast<const double*>(p.A), static_cast<const double*>(p.B), p.lda, p.ldb, p.Kp, m0, n0,
-                  smem, acc);
-    dmma_stage(smem, acc);
-    dmma_epilogue_rt(p.cdt, p.mode, p.e, m0, n0, smem);
   }
 }
 
@@ -353,18 +192,6 @@ cudaError_t launch_simt_mode(int mode, const GemmArgs& g, cudaStream_t s, dim3 g
 }
 
 template <int CDT>
-cudaError_t launch_dmma_mode(int mode, const GemmArgs& g, cudaStream_t s, dim3 grid) {
-  switch (mode) {
-    case OUT_REAL: dmma_gemm<CDT, OUT_REAL><<<grid, 128, 0, s>>>(g); break;
-    case OUT_RE_ONLY: dmma_gemm<CDT, OUT_RE_ONLY><<<grid, 128, 0, s>>>(g); break;
-    case OUT_ROWPAIR: dmma_gemm<CDT, OUT_ROWPAIR><<<grid, 128, 0, s>>>(g); break;
-    case OUT_COLPAIR: dmma_gemm<CDT, OUT_COLPAIR><<<grid, 128, 0, s>>>(g); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-template <int CDT>
 cudaError_t launch_for_c(int method, int mode, const GemmArgs& g, cudaStream_t s) {
   const TileCfg t = tile_cfg(method);
   const int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
@@ -377,7 +204,7 @@ cudaError_t launch_for_c(int method, int mode, const GemmArgs& g, cudaStream_t s
   switch (method) {
     case MXG_METHOD_FFMA: return launch_simt_mode<float, 4, CDT>(mode, g, s, grid);
     case MXG_METHOD_DFMA: return launch_simt_mode<double, 2, CDT>(mode, g, s, grid);
-    case MXG_METHOD_DMMA: return launch_dmma_mode<CDT>(mode, g, s, grid);
+    case MXG_METHOD_DMMA: return launch_dmma(mode, CDT, g, s, grid);
   }
   return cudaErrorInvalidValue;
 }
@@ -388,7 +215,7 @@ TileCfg tile_cfg(int method) {
   switch (method) {
     case MXG_METHOD_FFMA: return {128, 128, 8};
     case MXG_METHOD_DFMA: return {64, 64, 8};
-    case MXG_METHOD_DMMA: return {DM_T, DM_T, DM_TK};
+    case MXG_METHOD_DMMA: return {64, 64, 16};
     case MXG_METHOD_TF32X3: return {128, 128, 32};
     case MXG_METHOD_BF16X3: return {128, 128, 64};
   }
@@ -400,7 +227,6 @@ int variant_tile(int variant) {
     case VAR_FFMA_128: return 128;
     case VAR_FFMA_64: return 64;
     case VAR_DFMA_64: return 64;
-    case VAR_DFMA_32: return 32;
     case VAR_DMMA_64: return 64;
   }
   return 0;
@@ -424,8 +250,7 @@ cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const Group
     case VAR_FFMA_128: simt_gemm_grouped<float, 4><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_FFMA_64: simt_gemm_grouped<float, 2><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_DFMA_64: simt_gemm_grouped<double, 2><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
-    case VAR_DFMA_32: simt_gemm_grouped<double, 1><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
-    case VAR_DMMA_64: dmma_gemm_grouped<<<grid, 128, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_DMMA_64: return launch_dmma_grouped(probs, tiles, ntiles, counter, sched, grid, s);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -438,8 +263,7 @@ int grouped_blocks_per_sm(int variant) {
     case VAR_FFMA_128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 4>, 256, 0); break;
     case VAR_FFMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 2>, 256, 0); break;
     case VAR_DFMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 2>, 256, 0); break;
-    case VAR_DFMA_32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 1>, 256, 0); break;
-    case VAR_DMMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dmma_gemm_grouped, 128, 0); break;
+    case VAR_DMMA_64: return dmma_grouped_blocks_per_sm();
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -10,7 +10,7 @@ enum GroupVariant : int {
   VAR_FFMA_128 = 0,   // FP32 FFMA, 128 x 128
   VAR_FFMA_64 = 1,    // FP32 FFMA, 64 x 64
   VAR_DFMA_64 = 2,    // FP64 DFMA, 64 x 64
-  VAR_DFMA_32 = 3,    // reserved
+  VAR_DFMA_32 = 3,    // reserved (not built: the complex epilogue needs row pairs per thread)
   VAR_DMMA_64 = 4     // FP64 DMMA, 64 x 64
 };
 
@@ -33,7 +33,24 @@ struct GroupTile {
   int tm, tn;          // tile coordinates in units of the variant's tile
 };
 
+#ifdef __CUDACC__
+// Fetch the next work-list index for the whole CTA (dynamic schedule: one atomic per
+// tile on the bucket's counter; static schedule: CTA b takes b, b + grid, ...).
+__device__ __forceinline__ int next_tile(int* counter, int* slot, int prev, int sched) {
+  if (sched == SCHED_STATIC) return prev < 0 ? static_cast<int>(blockIdx.x) : prev + static_cast<int>(gridDim.x);
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+  __syncthreads();
+  return *slot;
+}
+
+#endif
+
 int variant_tile(int variant);
+cudaError_t launch_dmma(int mode, int cdt, const GemmArgs& g, cudaStream_t s, dim3 grid);
+cudaError_t launch_dmma_grouped(const GroupProb* probs, const GroupTile* tiles, int ntiles, int* counter, int sched,
+                                int grid, cudaStream_t s);
+int dmma_grouped_blocks_per_sm();
 int grouped_blocks_per_sm(int variant);
 cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const GroupTile* tiles, int ntiles,
                                 int* counter, int sched, int grid, cudaStream_t s);
