@@ -216,8 +216,8 @@ TileCfg tile_cfg(int method) {
     case MXG_METHOD_FFMA: return {128, 128, 8};
     case MXG_METHOD_DFMA: return {64, 64, 8};
     case MXG_METHOD_DMMA: return {64, 64, 16};
-    case MXG_METHOD_TF32X3: return {128, 128, 32};
-    case MXG_METHOD_BF16X3: return {128, 128, 64};
+    case MXG_METHOD_TF32X3: return {128, 256, 16};   // tcgen05 tile 128 x 256, 64-byte k rows
+    case MXG_METHOD_BF16X3: return {128, 256, 32};
   }
   return {128, 128, 8};
 }

@@ -5,17 +5,20 @@
 // accumulated in FP32 in tensor memory over the whole K' (Sec. 6.3: one cast per
 // element of C), followed by the same fused epilogue as the other contractions.
 //
-// One CTA computes a 128 x 128 tile of P:
-//   warp 0      TMA producer: per k-block loads A_hi, A_lo, B_hi, B_lo tiles (128 rows
-//               x 128 bytes, 128-byte swizzle) into a 3-stage shared-memory ring;
-//   warp 1      allocates the TMEM accumulator (128 lanes x 128 FP32 columns) and one
-//               elected lane issues tcgen05.mma (M=128, N=128) for the three products;
-//               tcgen05.commit frees each stage and finally signals the epilogue;
+// Persistent kernel, one CTA per SM, tiles of 128 x 256 of P walked in a grouped order
+// (GM m-tiles at a time) so that concurrently running CTAs share operand panels in L2:
+//   warp 0      TMA producer: per k-block of 64 bytes loads A_hi, A_lo (128 rows) and
+//               B_hi, B_lo (256 rows) with the 64-byte swizzle into a 4-stage ring;
+//   warp 1      owns the TMEM allocation (two 128 x 256 FP32 accumulators, 512
+//               columns); one lane issues tcgen05.mma (M = 128, N = 256) for the three
+//               products, frees each stage with tcgen05.commit and hands a finished
+//               accumulator to the epilogue;
 //   warps 2..5  epilogue: tcgen05.ld the accumulator (warp w reads TMEM lanes
-//               32*(w%4)..), pair rows or columns for complex C, alpha/beta, store.
-// Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel sets
-// the handle's error word, skips the store, waits (bounded) for its own TMA copies in
-// flight, frees its TMEM and returns.
+//               32*(w%4)..), pair rows or columns for complex C, alpha/beta, store,
+//               then release the accumulator -- overlapping the next tile's main loop.
+// Every mbarrier wait is bounded in time (%globaltimer). On expiry the CTA sets the
+// error word and an abort flag, skips its stores, waits (bounded) for its own TMA
+// copies and MMAs in flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,19 +29,21 @@
 namespace mxg {
 
 struct TcArgs {
-  int64_t Mp, Np, Kp;   // padded real problem (multiples of 128, 128, BK)
+  int64_t Mp, Np, Kp;   // padded real problem (multiples of 128, 256, BK)
   EpiArgs e;
   int* err;             // device error word set on a wait timeout (may be null)
 };
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_STAGES = 3;
-constexpr uint32_t TILE_A = TC_BM * 128;                  // bytes: 128 rows x 128 B
-constexpr uint32_t TILE_B = TC_BN * 128;
-constexpr uint32_t STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4, TC_GM = 16;
+constexpr uint32_t ROWB = 64;                              // bytes of K per tile row (64-byte swizzle)
+constexpr uint32_t TILE_A = TC_BM * ROWB;                  // 8 KB
+constexpr uint32_t TILE_B = TC_BN * ROWB;                  // 16 KB
+constexpr uint32_t STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // A_hi, A_lo, B_hi, B_lo: 48 KB
+constexpr uint32_t NBARS = 2 * TC_STAGES + 2 + 2 + 1;      // full, empty, acc_full, acc_empty, drain
 constexpr uint32_t TC_SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = TC_BN;
+constexpr uint32_t TMEM_COLS = 2 * TC_BN;                  // two accumulators
 constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -55,6 +60,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -66,14 +74,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on the phase of the given parity. Returns false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait on the phase of the given parity; false after kWaitNs or when another
+// role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 255) == 0 && gtimer() - t0 > kWaitNs) return false;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kWaitNs) return false;
+    }
   }
+}
+// Bounded wait that ignores the abort flag (used to drain the CTA's own work).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
   asm volatile(
@@ -81,17 +99,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
-// Shared-memory matrix descriptor for a K-major tile written by TMA with the 128-byte
-// swizzle: rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the 64-byte
+// swizzle: rows of 64 bytes, 8-row swizzle atoms 512 bytes apart (stride byte
 // offset), leading byte offset unused for this layout (encoded as 1), descriptor
-// version 1, layout type 2 (128-byte swizzle).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// version 1, layout type 4 (64-byte swizzle).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr >> 4) & 0x3fff);
   d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
   d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(2) << 61;
+  d |= static_cast<uint64_t>(4) << 61;
   return d;
 }
 // Instruction descriptor (kind::f16 / kind::tf32): D in FP32, A and B of the given
@@ -117,6 +135,9 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t adesc, uint64_
         ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
   }
 }
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
@@ -131,28 +152,40 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Tile t of the grouped order -> (m tile, n tile): groups of TC_GM m-tiles, n fastest
+// within a group column.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int* tm, int* tn) {
+  const int per_group = TC_GM * tiles_n;
+  const int g = t / per_group, r = t - g * per_group;
+  const int gm0 = g * TC_GM;
+  const int gsz = min(TC_GM, tiles_m - gm0);
+  *tm = gm0 + r % gsz;
+  *tn = r / gsz;
+}
+
 template <int SPLIT, int CDT, int MODE>
 __global__ void __launch_bounds__(192, 1)
 tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
   constexpr int ELEM = (SPLIT == SPLIT_BF16) ? 2 : 4;
-  constexpr int BK = 128 / ELEM;            // k elements per 128-byte row
-  constexpr int KSTEP = 32 / ELEM;          // k elements per MMA (16 bf16 / 8 tf32)
+  constexpr int BK = ROWB / ELEM;           // k elements per 64-byte row
+  constexpr int KSTEPS = ROWB / 32;         // MMAs per row (each consumes 32 bytes of K)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base = (raw + 1023u) & ~1023u;                     // 1024-aligned tiles
+  const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gen_base = smem_raw + (base - raw);
-  const uint32_t bars = base + TC_STAGES * STAGE_BYTES;             // full[S], empty[S], acc
-  uint64_t* bar_ptr = reinterpret_cast<uint64_t*>(gen_base + TC_STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 2 * TC_STAGES + 1);
+  const uint32_t bars = base + TC_STAGES * STAGE_BYTES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * STAGE_BYTES + 8 * NBARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (TC_STAGES + s); };
-  const uint32_t acc_bar = bars + 8u * (2 * TC_STAGES);
+  auto acc_full = [&](int b) { return bars + 8u * (2 * TC_STAGES + b); };
+  auto acc_empty = [&](int b) { return bars + 8u * (2 * TC_STAGES + 2 + b); };
+  const uint32_t drain_bar = bars + 8u * (2 * TC_STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * TC_BM;
-  const int64_t n0 = static_cast<int64_t>(blockIdx.y) * TC_BN;
+  const int tiles_m = static_cast<int>(g.Mp / TC_BM), tiles_n = static_cast<int>(g.Np / TC_BN);
+  const int ntiles = tiles_m * tiles_n;
   const int nkb = static_cast<int>(g.Kp / BK);
 
   if (threadIdx.x == 0) {
@@ -160,7 +193,11 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    mbar_init(acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 4);   // one arrival per epilogue warp
+    }
+    mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -174,98 +211,120 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  auto fail = [&]() {
+    if (g.err) atomicExch(g.err, 1);
+    *abort_flag = 1;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
+      uint32_t it = 0;
       bool ok = true;
-      int issued = 0;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = static_cast<uint32_t>(kb / TC_STAGES) & 1u;
-        if (!mbar_wait(empty(s), ph ^ 1u)) { ok = false; break; }
-        if (*abort_flag) { ok = false; break; }
-        const uint32_t st = base + s * STAGE_BYTES;
-        mbar_expect_tx(full(s), STAGE_BYTES);
-        const int32_t kx = kb * BK;
-        tma_load_2d(st, &mAh, kx, static_cast<int32_t>(m0), full(s));
-        tma_load_2d(st + TILE_A, &mAl, kx, static_cast<int32_t>(m0), full(s));
-        tma_load_2d(st + 2 * TILE_A, &mBh, kx, static_cast<int32_t>(n0), full(s));
-        tma_load_2d(st + 2 * TILE_A + TILE_B, &mBl, kx, static_cast<int32_t>(n0), full(s));
-        issued = kb + 1;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+        const int32_t ym = tm * TC_BM, yn = tn * TC_BN;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = static_cast<int>(it % TC_STAGES);
+          const uint32_t use = it / TC_STAGES;
+          if (!mbar_wait(empty(s), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          const uint32_t st = base + s * STAGE_BYTES;
+          mbar_expect_tx(full(s), STAGE_BYTES);
+          const int32_t kx = kb * BK;
+          tma_load_2d(st, &mAh, kx, ym, full(s));
+          tma_load_2d(st + TILE_A, &mAl, kx, ym, full(s));
+          tma_load_2d(st + 2 * TILE_A, &mBh, kx, yn, full(s));
+          tma_load_2d(st + 2 * TILE_A + TILE_B, &mBl, kx, yn, full(s));
+        }
       }
       if (!ok) {
-        if (g.err) atomicExch(g.err, 1);
-        *abort_flag = 1;
-        // wait (bounded) for this thread's own copies still in flight
-        for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
-          mbar_wait(full(kb % TC_STAGES), static_cast<uint32_t>(kb / TC_STAGES) & 1u);
+        fail();
+        // wait (bounded) for this thread's own copies: the last use of every stage
+        for (uint32_t j = (it > TC_STAGES ? it - TC_STAGES : 0); j < it; ++j)
+          mbar_drain(full(j % TC_STAGES), (j / TC_STAGES) & 1u);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      uint32_t it = 0;
       bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % TC_STAGES;
-        if (!mbar_wait(full(s), static_cast<uint32_t>(kb / TC_STAGES) & 1u) || *abort_flag) {
-          ok = false;
-          break;
-        }
+      int j = 0;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+        const int b = j & 1;
+        if (!mbar_wait(acc_empty(b), (static_cast<uint32_t>(j >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = base + s * STAGE_BYTES;
-        const uint32_t a_hi = st, a_lo = st + TILE_A, b_hi = st + 2 * TILE_A, b_lo = b_hi + TILE_B;
+        const uint32_t acc_tmem = tmem + static_cast<uint32_t>(b * TC_BN);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = static_cast<int>(it % TC_STAGES);
+          if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint32_t a_hi = st, a_lo = st + TILE_A, b_hi = st + 2 * TILE_A, b_lo = b_hi + TILE_B;
 #pragma unroll
-        for (int kk = 0; kk < BK / KSTEP; ++kk) {
-          const uint32_t off = kk * 32;   // bytes along K inside the 128-byte row
-          const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-          mma_issue<SPLIT>(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), first);
-          mma_issue<SPLIT>(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
-          mma_issue<SPLIT>(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+          for (int kk = 0; kk < KSTEPS; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_issue<SPLIT>(acc_tmem, sw64_desc(a_hi + off), sw64_desc(b_hi + off), first);
+            mma_issue<SPLIT>(acc_tmem, sw64_desc(a_hi + off), sw64_desc(b_lo + off), 1u);
+            mma_issue<SPLIT>(acc_tmem, sw64_desc(a_lo + off), sw64_desc(b_hi + off), 1u);
+          }
+          mma_commit(empty(s));
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     ::"r"(empty(s)) : "memory");
+        if (!ok) break;
+        mma_commit(acc_full(b));
       }
-      if (!ok) {
-        if (g.err) atomicExch(g.err, 1);
-        *abort_flag = 1;
-      }
-      // signal the epilogue once every issued MMA has completed
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   ::"r"(acc_bar) : "memory");
+      if (!ok) fail();
+      // every MMA this thread issued has completed once the drain barrier flips
+      mma_commit(drain_bar);
+      mbar_drain(drain_bar, 0);
     }
   } else {
     // epilogue warps 2..5: TMEM lane quarter q = warp % 4
     const int q = warp & 3;
-    const bool ok = mbar_wait(acc_bar, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok && g.err) atomicExch(g.err, 1);
-    const bool store = __all_sync(0xffffffffu, ok && !*abort_flag);
-    const int64_t row = m0 + 32 * q + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c0), v);
-      if (!store) continue;
-      if constexpr (MODE == OUT_ROWPAIR) {
-        // rows 2i and 2i+1 sit in lanes 2l and 2l+1: the even lane takes even
-        // columns, the odd lane odd columns
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float mine = __uint_as_float(v[j]);
-          const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-          if ((j & 1) == (lane & 1)) {
-            const float pr = (lane & 1) ? other : mine, pi = (lane & 1) ? mine : other;
-            epi_store<float, CDT, MODE>(g.e, row >> 1, n0 + c0 + j, pr, pi);
-          }
-        }
-      } else if constexpr (MODE == OUT_COLPAIR) {
-#pragma unroll
-        for (int j = 0; j < 32; j += 2)
-          epi_store<float, CDT, MODE>(g.e, row, (n0 + c0 + j) >> 1, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          epi_store<float, CDT, MODE>(g.e, row, n0 + c0 + j, __uint_as_float(v[j]), 0.0f);
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      const int b = j & 1;
+      const bool ok = mbar_wait(acc_full(b), static_cast<uint32_t>(j >> 1) & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, ok && !*abort_flag)) {
+        if (lane == 0 && !ok) fail();
+        break;
       }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t m0 = static_cast<int64_t>(tm) * TC_BM, n0 = static_cast<int64_t>(tn) * TC_BN;
+      const int64_t row = m0 + 32 * q + lane;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b * TC_BN);
+#pragma unroll 1
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
+        if constexpr (MODE == OUT_ROWPAIR) {
+          // rows 2i and 2i+1 sit in lanes 2l and 2l+1: the even lane takes even
+          // columns, the odd lane odd columns
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const float mine = __uint_as_float(v[jj]);
+            const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+            if ((jj & 1) == (lane & 1)) {
+              const float pr = (lane & 1) ? other : mine, pi = (lane & 1) ? mine : other;
+              epi_store<float, CDT, MODE>(g.e, row >> 1, n0 + c0 + jj, pr, pi);
+            }
+          }
+        } else if constexpr (MODE == OUT_COLPAIR) {
+#pragma unroll
+          for (int jj = 0; jj < 32; jj += 2)
+            epi_store<float, CDT, MODE>(g.e, row, (n0 + c0 + jj) >> 1, __uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            epi_store<float, CDT, MODE>(g.e, row, n0 + c0 + jj, __uint_as_float(v[jj]), 0.0f);
+        }
+      }
+      // release the accumulator to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(b));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -279,6 +338,7 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
+int g_num_sms = 0;
 
 bool get_encoder() {
   std::call_once(g_encode_once, [] {
@@ -294,16 +354,16 @@ bool get_encoder() {
 }
 
 // 2-D map over a K-major plane (rows x Kp elements, row pitch Kp elements), box
-// 128 rows x 128 bytes, 128-byte swizzle.
-bool make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp) {
+// (rows_box x 64 bytes), 64-byte swizzle.
+bool make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box) {
   const int elem = (split == SPLIT_BF16) ? 2 : 4;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(rows)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * elem};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem), 128u};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(ROWB / elem), rows_box};
   const cuuint32_t estr[2] = {1u, 1u};
   const CUresult r = g_encode(map, split == SPLIT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                               2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -313,7 +373,8 @@ cudaError_t launch_one(const CUtensorMap* maps, const TcArgs& g, cudaStream_t s)
   auto kern = tc_split_gemm<SPLIT, CDT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e != cudaSuccess) return e;
-  const dim3 grid(static_cast<unsigned>(g.Mp / TC_BM), static_cast<unsigned>(g.Np / TC_BN));
+  const int64_t ntiles = (g.Mp / TC_BM) * (g.Np / TC_BN);
+  const int grid = static_cast<int>(ntiles < g_num_sms ? ntiles : g_num_sms);
   kern<<<grid, 192, TC_SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], g);
   return cudaGetLastError();
 }
@@ -351,12 +412,19 @@ cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const pla
                            int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s) {
   if (!get_encoder()) return cudaErrorNotSupported;
   const int split = (method == MXG_METHOD_BF16X3) ? SPLIT_BF16 : SPLIT_TF32;
-  if (Mp % TC_BM || Np % TC_BN || Kp % (128 / (split == SPLIT_BF16 ? 2 : 4))) return cudaErrorInvalidValue;
-  if (Mp / TC_BM > 0x7fffffffLL || Np / TC_BN > 65535) return cudaErrorInvalidValue;
+  const int bk = static_cast<int>(ROWB) / (split == SPLIT_BF16 ? 2 : 4);
+  if (Mp % TC_BM || Np % TC_BN || Kp % bk) return cudaErrorInvalidValue;
+  if ((Mp / TC_BM) * (Np / TC_BN) > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (Mp == 0 || Np == 0) return cudaSuccess;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess || g_num_sms <= 0) return ce != cudaSuccess ? ce : cudaErrorInvalidValue;
+  }
   CUtensorMap maps[4];
-  if (!make_map(&maps[0], planes[0], split, Mp, Kp) || !make_map(&maps[1], planes[1], split, Mp, Kp) ||
-      !make_map(&maps[2], planes[2], split, Np, Kp) || !make_map(&maps[3], planes[3], split, Np, Kp))
+  if (!make_map(&maps[0], planes[0], split, Mp, Kp, TC_BM) || !make_map(&maps[1], planes[1], split, Mp, Kp, TC_BM) ||
+      !make_map(&maps[2], planes[2], split, Np, Kp, TC_BN) || !make_map(&maps[3], planes[3], split, Np, Kp, TC_BN))
     return cudaErrorInvalidValue;
   TcArgs g{Mp, Np, Kp, e, err};
   return split == SPLIT_BF16 ? launch_split<SPLIT_BF16>(c_dt, mode, maps, g, s)
