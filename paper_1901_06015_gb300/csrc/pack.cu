@@ -6,11 +6,11 @@
 // operand in full (zeros outside the logical extent), so the contraction kernels run
 // without bounds checks.
 //
-// A block handles a 32 (mn) x 32 (p) tile of logical elements: it reads the tile with
+// A block handles a 64 (mn) x 32 (p) tile of logical elements: it reads the tile with
 // the lanes along whichever source dimension has unit stride, keeps it in shared
-// memory, and writes the 32*fk x 32*fm packed sub-block with the lanes along the
-// packed operand's contiguous dimension, so both sides are coalesced for row-,
-// column- and (as far as possible) general storage.
+// memory, and writes the packed sub-block in 16-byte vectors along the packed
+// operand's contiguous dimension, so both sides are coalesced for row-, column- and
+// (as far as possible) general storage.
 #include <cuda_bf16.h>
 
 #include "mxg_internal.h"
@@ -37,6 +37,7 @@ __device__ __forceinline__ float tf32_rne(float x) {
 
 template <typename DT>
 __device__ __forceinline__ DT pattern_value(int pattern, int s, int t, DT xr, DT xi) {
+  // (for a real source the planner only uses PAT_RE, so xi is never read there)
   switch (pattern) {
     case PAT_SPLIT_MN: return t ? xi : xr;
     case PAT_SPLIT_K: return s ? xi : xr;
@@ -45,65 +46,120 @@ __device__ __forceinline__ DT pattern_value(int pattern, int s, int t, DT xr, DT
   }
 }
 
+constexpr int PK_MN = 64, PK_P = 32;   // logical tile: 64 (mn) x 32 (p) elements
+
 template <typename DT>
 struct PackSmem {
-  DT re[32][33];
-  DT im[32][33];
+  DT re[PK_P][PK_MN + 1];
+  DT im[PK_P][PK_MN + 1];
 };
 
-// One 32 (mn) x 32 (p) tile of logical elements starting at (mn0, p0): read it with
-// the lanes along the source's unit-stride dimension, keep it in shared memory, and
-// write the 32*fk x 32*fm packed sub-block with the lanes along the packed operand's
-// contiguous dimension. Ends with the block synchronised.
+template <int SPLIT, typename DT> struct OutVec;
+template <> struct OutVec<SPLIT_NONE, float> { static constexpr int n = 4; };
+template <> struct OutVec<SPLIT_NONE, double> { static constexpr int n = 2; };
+template <> struct OutVec<SPLIT_TF32, float> { static constexpr int n = 4; };
+template <> struct OutVec<SPLIT_BF16, float> { static constexpr int n = 8; };
+
+// One 64 (mn) x 32 (p) tile of logical elements starting at (mn0, p0): read it with
+// the lanes along the source's unit-stride dimension (8 independent loads per
+// thread), keep it in shared memory, and write the 32*fk x 64*fm packed sub-block as
+// 16-byte vectors along the packed operand's contiguous dimension (MN for the SIMT
+// layout, K for the tensor-core planes). Padded extents are multiples of the vector
+// width, so a vector is either wholly inside or wholly outside them. Ends with the
+// block synchronised.
 template <int SDT, typename DT, int LAYOUT, int SPLIT>
 __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_t p0, PackSmem<DT>& sm) {
   using ST = typename SrcT<SDT>::T;
   constexpr bool SC = SrcT<SDT>::cplx;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  constexpr int V = OutVec<SPLIT, DT>::n;
+  const int t = threadIdx.x;
   const bool unit_mn = (a.smn == 1);
   const int fk = (a.pattern == PAT_SPLIT_K || a.pattern == PAT_ONE_E) ? 2 : 1;
   const int fm = (a.pattern == PAT_SPLIT_MN || a.pattern == PAT_ONE_E) ? 2 : 1;
-  for (int r = ty; r < 32; r += 8) {
-    const int lm = unit_mn ? tx : r;
-    const int lp = unit_mn ? r : tx;
+  ST vr_[8], vi_[8];
+  int lm_[8], lp_[8];
+  bool in_[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int lm = unit_mn ? (t & 63) : ((t >> 5) + 8 * i);
+    const int lp = unit_mn ? ((t >> 6) + 4 * i) : (t & 31);
     const int64_t mn = mn0 + lm, p = p0 + lp;
-    DT vr = DT(0), vi = DT(0);
-    if (mn < a.MN && p < a.K) {
-      const ST* s = static_cast<const ST*>(a.src) + (mn * a.smn + p * a.sk) * (SC ? 2 : 1);
-      vr = static_cast<DT>(s[0]);
-      if constexpr (SC) vi = static_cast<DT>(a.conj ? -s[1] : s[1]);
+    lm_[i] = lm; lp_[i] = lp;
+    in_[i] = (mn < a.MN && p < a.K);
+    vr_[i] = ST(0); vi_[i] = ST(0);
+    if (in_[i]) {
+      const ST* sp = static_cast<const ST*>(a.src) + (mn * a.smn + p * a.sk) * (SC ? 2 : 1);
+      vr_[i] = __ldg(sp);
+      if constexpr (SC) vi_[i] = __ldg(sp + 1);
     }
-    sm.re[lp][lm] = vr;
-    sm.im[lp][lm] = vi;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    sm.re[lp_[i]][lm_[i]] = static_cast<DT>(vr_[i]);
+    if constexpr (SC) {   // a real source only ever uses the RE pattern
+      const DT im = static_cast<DT>(vi_[i]);
+      sm.im[lp_[i]][lm_[i]] = a.conj ? -im : im;
+    }
   }
   __syncthreads();
-  const int nk_out = 32 * fk, nm_out = 32 * fm, total = nk_out * nm_out;
-  for (int idx = threadIdx.x; idx < total; idx += 256) {
-    int r, c;  // r: packed K index in the tile, c: packed MN index in the tile
-    if constexpr (LAYOUT == LAYOUT_MN_MAJOR) {
-      r = idx / nm_out;
-      c = idx - r * nm_out;
-    } else {
-      c = idx / nk_out;
-      r = idx - c * nk_out;
+  const int nk_out = PK_P * fk, nm_out = PK_MN * fm;
+  if constexpr (LAYOUT == LAYOUT_MN_MAJOR) {
+    const int vec_per_row = nm_out / V, total = nk_out * vec_per_row;
+    for (int idx = t; idx < total; idx += 256) {
+      const int r = idx / vec_per_row, c0 = (idx - r * vec_per_row) * V;
+      const int64_t kk = p0 * fk + r, mm = mn0 * fm + c0;
+      if (kk >= a.Kp || mm >= a.MNp) continue;
+      const int lp = r / fk, s = r - lp * fk;
+      DT v[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int c = c0 + u, lm = c / fm, tt = c - lm * fm;
+        v[u] = SC ? pattern_value<DT>(a.pattern, s, tt, sm.re[lp][lm], sm.im[lp][lm]) : sm.re[lp][lm];
+      }
+      DT* dst = static_cast<DT*>(a.dst) + kk * a.ld + mm;
+      if constexpr (V == 4) *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      else *reinterpret_cast<double2*>(dst) = make_double2(v[0], v[1]);
     }
-    const int64_t kk = p0 * fk + r, mm = mn0 * fm + c;
-    if (kk >= a.Kp || mm >= a.MNp) continue;
-    const int lp = r / fk, s = r - lp * fk, lm = c / fm, t = c - lm * fm;
-    const DT v = pattern_value<DT>(a.pattern, s, t, sm.re[lp][lm], sm.im[lp][lm]);
-    const int64_t off = (LAYOUT == LAYOUT_MN_MAJOR) ? kk * a.ld + mm : mm * a.ld + kk;
-    if constexpr (SPLIT == SPLIT_NONE) {
-      static_cast<DT*>(a.dst)[off] = v;
-    } else if constexpr (SPLIT == SPLIT_TF32) {
-      const float hi = tf32_rne(static_cast<float>(v));
-      const float lo = tf32_rne(static_cast<float>(v) - hi);
-      static_cast<float*>(a.dst)[off] = hi;
-      static_cast<float*>(a.dst_lo)[off] = lo;
-    } else {
-      const __nv_bfloat16 hi = __float2bfloat16_rn(static_cast<float>(v));
-      const __nv_bfloat16 lo = __float2bfloat16_rn(static_cast<float>(v) - __bfloat162float(hi));
-      static_cast<__nv_bfloat16*>(a.dst)[off] = hi;
-      static_cast<__nv_bfloat16*>(a.dst_lo)[off] = lo;
+  } else {
+    const int vec_per_row = nk_out / V, total = nm_out * vec_per_row;
+    for (int idx = t; idx < total; idx += 256) {
+      const int c = idx / vec_per_row, r0 = (idx - c * vec_per_row) * V;
+      const int64_t kk = p0 * fk + r0, mm = mn0 * fm + c;
+      if (kk >= a.Kp || mm >= a.MNp) continue;
+      const int lm = c / fm, tt = c - lm * fm;
+      float hi[V], lo[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int r = r0 + u, lp = r / fk, s = r - lp * fk;
+        const float x = static_cast<float>(SC ? pattern_value<DT>(a.pattern, s, tt, sm.re[lp][lm], sm.im[lp][lm])
+                                              : sm.re[lp][lm]);
+        if constexpr (SPLIT == SPLIT_TF32) {
+          hi[u] = tf32_rne(x);
+          lo[u] = tf32_rne(x - hi[u]);
+        } else {
+          const __nv_bfloat16 h = __float2bfloat16_rn(x);
+          hi[u] = __bfloat162float(h);
+          lo[u] = x - hi[u];
+        }
+      }
+      const int64_t off = mm * a.ld + kk;
+      if constexpr (SPLIT == SPLIT_TF32) {
+        *reinterpret_cast<float4*>(static_cast<float*>(a.dst) + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(static_cast<float*>(a.dst_lo) + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      } else {
+        uint4 ph, pl;
+        uint32_t* h32 = reinterpret_cast<uint32_t*>(&ph);
+        uint32_t* l32 = reinterpret_cast<uint32_t*>(&pl);
+#pragma unroll
+        for (int u = 0; u < V; u += 2) {
+          const __nv_bfloat162 hh = __floats2bfloat162_rn(hi[u], hi[u + 1]);   // exact: already bf16
+          const __nv_bfloat162 ll = __floats2bfloat162_rn(lo[u], lo[u + 1]);   // RN of x - hi
+          h32[u / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+          l32[u / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+        }
+        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst) + off) = ph;
+        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst_lo) + off) = pl;
+      }
     }
   }
   __syncthreads();
@@ -112,8 +168,8 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
 template <int SDT, typename DT, int LAYOUT, int SPLIT>
 __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, int64_t ntile_p) {
   __shared__ PackSmem<DT> sm;
-  const int64_t mn0 = static_cast<int64_t>(blockIdx.x) * 32;
-  for (int64_t tp = blockIdx.y; tp < ntile_p; tp += gridDim.y) pack_tile<SDT, DT, LAYOUT, SPLIT>(a, mn0, tp * 32, sm);
+  const int64_t mn0 = static_cast<int64_t>(blockIdx.x) * PK_MN;
+  for (int64_t tp = blockIdx.y; tp < ntile_p; tp += gridDim.y) pack_tile<SDT, DT, LAYOUT, SPLIT>(a, mn0, tp * PK_P, sm);
 }
 
 // Grouped pack: block b packs tile (b - tile_start[t]) of task t, where t is found by a
@@ -132,8 +188,8 @@ __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __res
   const PackArgs a = tasks[lo];
   const int64_t local = b - tile_start[lo];
   const int fm = pat_fm(a.pattern);
-  const int64_t tiles_mn = (a.MNp / fm + 31) / 32;
-  const int64_t mn0 = (local % tiles_mn) * 32, p0 = (local / tiles_mn) * 32;
+  const int64_t tiles_mn = (a.MNp / fm + PK_MN - 1) / PK_MN;
+  const int64_t mn0 = (local % tiles_mn) * PK_MN, p0 = (local / tiles_mn) * PK_P;
   switch (a.src_dt) {
     case MXG_S: pack_tile<MXG_S, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
     case MXG_D: pack_tile<MXG_D, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
@@ -145,7 +201,7 @@ __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __res
 template <int SDT>
 cudaError_t launch_src(const PackArgs& a, int comp_double, cudaStream_t s) {
   const int fk = pat_fk(a.pattern), fm = pat_fm(a.pattern);
-  const int64_t ntm = (a.MNp / fm + 31) / 32, ntp = (a.Kp / fk + 31) / 32;
+  const int64_t ntm = (a.MNp / fm + PK_MN - 1) / PK_MN, ntp = (a.Kp / fk + PK_P - 1) / PK_P;
   if (ntm <= 0 || ntp <= 0) return cudaSuccess;
   if (ntm > 0x7fffffffLL) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(ntm), static_cast<unsigned>(ntp < 65535 ? ntp : 65535));
@@ -166,7 +222,7 @@ cudaError_t launch_src(const PackArgs& a, int comp_double, cudaStream_t s) {
 
 int64_t pack_tiles(const PackArgs& a) {
   const int fk = pat_fk(a.pattern), fm = pat_fm(a.pattern);
-  return ((a.MNp / fm + 31) / 32) * ((a.Kp / fk + 31) / 32);
+  return ((a.MNp / fm + PK_MN - 1) / PK_MN) * ((a.Kp / fk + PK_P - 1) / PK_P);
 }
 
 cudaError_t launch_pack_grouped(const PackArgs* tasks, const int64_t* tile_start, int ntasks, int64_t ntiles,
