@@ -320,6 +320,13 @@ int mxgemm_noalloc(void* stream, int method, int transa, int transb,
                    void* C, int dtC, int64_t rsC, int64_t csC,
                    int comp_prec);
 
+/* Self-test of the device-side wait limit: launches one kernel that waits on an
+ * mbarrier nothing will ever arrive on, for at most `seconds` (0 < seconds <= 10), on
+ * h's stream. Returns MXG_ETIMEOUT when the wait ran out and reported it through the
+ * error word (the expected outcome; the word is cleared again), MXG_OK if it did not
+ * report, or an error status. The GPU context stays usable. */
+int mxg_selftest_wait_timeout(mxg_handle h, double seconds);
+
 /* Human-readable text of a status code (static storage). */
 const char* mxg_strerror(int status);
 

@@ -401,6 +401,20 @@ int mxg_phase_times(mxg_handle h, double* pack_ms, double* contraction_ms, int64
   return MXG_OK;
 }
 
+int mxg_selftest_wait_timeout(mxg_handle h, double seconds) {
+  if (!h || !(seconds > 0.0) || seconds > 10.0) return MXG_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaError_t e = launch_wait_timeout_probe(h->dev_err, seconds, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int v = 0;
+  e = cudaMemcpyAsync(&v, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return v ? MXG_ETIMEOUT : MXG_OK;
+}
+
 int mxg_check_device_error(mxg_handle h, int* flag) {
   if (!h || !flag) return MXG_EINVAL;
   int v = 0;

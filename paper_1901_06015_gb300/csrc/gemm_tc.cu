@@ -335,6 +335,23 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing will
+// arrive on, for at most limit_ns, then records the timeout in the error word.
+__global__ void wait_timeout_probe(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(b, 0)) {
+    if (gtimer() - t0 > limit_ns) {
+      atomicExch(err, 1);
+      return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -406,6 +423,11 @@ cudaError_t launch_split(int c_dt, int mode, const CUtensorMap* maps, const TcAr
 }
 
 }  // namespace
+
+cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s) {
+  wait_timeout_probe<<<1, 32, 0, s>>>(err, static_cast<unsigned long long>(seconds * 1e9));
+  return cudaGetLastError();
+}
 
 // planes: A_hi, A_lo (Mp x Kp, K-major), B_hi, B_lo (Np x Kp, K-major)
 cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,

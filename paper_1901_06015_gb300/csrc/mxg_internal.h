@@ -86,6 +86,8 @@ TileCfg tile_cfg(int method);
 cudaError_t launch_pack(const PackArgs& a, int comp_double, cudaStream_t s);
 cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_scale_c(const EpiArgs& e, int c_dt, cudaStream_t s);
+// Bounded-wait self-test: a wait nothing will satisfy, limited to `seconds`.
+cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s);
 // Split-precision tensor-core contraction: planes = {A_hi, A_lo, B_hi, B_lo}, K-major.
 cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const planes[4], int64_t Mp,
                            int64_t Np, int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s);

@@ -121,6 +121,8 @@ def lib():
             L.mxg_set_phase_timing.argtypes = [_vp, _i32]
             L.mxg_phase_times.restype = _i32
             L.mxg_phase_times.argtypes = [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]
+            L.mxg_selftest_wait_timeout.restype = _i32
+            L.mxg_selftest_wait_timeout.argtypes = [_vp, _dbl]
             L.mxg_strerror.restype = ctypes.c_char_p
             L.mxg_strerror.argtypes = [_i32]
             L.mxg_last_cuda_error.restype = _i32
@@ -213,6 +215,10 @@ class Handle:
         if st:
             raise MxgError(st, "mxg_check_device_error")
         return int(f.value)
+
+    def selftest_wait_timeout(self, seconds=0.05):
+        """Status of the bounded-wait self-test (MXG_ETIMEOUT = 5 is the expected one)."""
+        return lib().mxg_selftest_wait_timeout(self.h, float(seconds))
 
     def set_phase_timing(self, on):
         st = lib().mxg_set_phase_timing(self.h, 1 if on else 0)

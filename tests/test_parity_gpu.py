@@ -144,3 +144,16 @@ def test_default_entry_point_mxgemm():
     torch.cuda.synchronize()
     err, _ = normwise_error("czsc", dC.cpu().numpy(), ref, A, B, C0, 1.5, -0.5)
     assert err <= tolerance("czss", 90)
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives():
+    """A device wait that nothing satisfies runs out after its limit, reports
+    MXG_ETIMEOUT through the handle's error word, and the context stays usable."""
+    import paper_1901_06015_gb300 as mx
+    h = mx.Handle()
+    h.set_stream(torch.cuda.current_stream())
+    assert h.selftest_wait_timeout(0.02) == 5
+    assert h.check_device_error() == 0          # the self-test cleared the word
+    A, B, C0 = synth.problem(13, "ssss", 64, 64, 64)
+    _check("ssss", A, B, C0, 1.0, 0.0, method="bf16x3")
+    h.close()
