@@ -128,6 +128,19 @@ def traffic_per_launch(kernel):
     return d.get("dram_bytes_per_launch_at_bench_size")
 
 
+def aggregate_over_ranks(dist, t_ms, flops, device=None):
+    """Whole-job numbers of a replicas-only run: the slowest rank's time and the sum of
+    the ranks' useful flops (no data-path collective: only this reduction of two
+    scalars). Works with any torch.distributed backend (NCCL on GPUs, gloo in tests)."""
+    import torch
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    f = torch.tensor([float(flops)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(f[0])
+
+
 # ------------------------------------------------------------------ CPU (oracle) arm
 def oracle_sample(step, n, bm, bn, seed=123):
     """Time the oracle on one bm x bn block of C (full k = n) for each of the step's
@@ -279,13 +292,7 @@ def run_ours(args):
 
     flops_step = sum(2.0 * n ** 3 * R for _, R in step_combos(0))
     my_flops = flops_step * args.steps
-    t_max = ms
-    tot_flops = my_flops
-    if dist is not None:
-        tt = torch.tensor([ms, my_flops], dtype=torch.float64, device=dev)
-        mx_t = tt.clone(); dist.all_reduce(mx_t[:1], op=dist.ReduceOp.MAX)
-        sm_f = tt.clone(); dist.all_reduce(sm_f[1:], op=dist.ReduceOp.SUM)
-        t_max, tot_flops = float(mx_t[0]), float(sm_f[1])
+    t_max, tot_flops = aggregate_over_ranks(dist, ms, my_flops, dev)
     value = tot_flops / (t_max / 1e3) / 1e9
 
     # per-combo GFLOPS (this rank)
@@ -348,10 +355,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         ems = e0.elapsed_time(e1)
-        if dist is not None:
-            tt = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt[0])
+        ems, _ = aggregate_over_ranks(dist, ems, 0.0, dev)
         e2e = {"value": tot_flops / (ems / 1e3) / 1e9, "unit": "GFLOPS",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
