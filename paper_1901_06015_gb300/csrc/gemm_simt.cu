@@ -36,44 +36,72 @@ __device__ __forceinline__ void unpack(const typename VecT<T, H>::V& v, T* o) {
   else { o[0] = v; }
 }
 
+constexpr int SIMT_STAGES = 4;
+
 template <typename T, int H>
 struct SimtSmem {
   static constexpr int TM = 32 * H, TK = 8;
-  __align__(16) T As[2][TK][TM];
-  __align__(16) T Bs[2][TK][TM];
+  __align__(16) T As[SIMT_STAGES][TK][TM];
+  __align__(16) T Bs[SIMT_STAGES][TK][TM];
 };
 
-// Main loop of one 32H x 32H tile at (m0, n0); leaves the accumulators in acc.
+// Asynchronous global -> shared copy of one vector of BYTES (16 or 8) bytes; both
+// addresses must be BYTES-aligned.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  static_assert(BYTES == 16 || BYTES == 8, "vector copies only");
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Main loop of one 32H x 32H tile at (m0, n0); leaves the accumulators in acc. The
+// packed k-tiles stream global -> shared with cp.async through a SIMT_STAGES-deep ring
+// (each thread copies one vector -- H elements, 16 or 8 bytes -- of A' and one of B'
+// per k-tile; each row of a k-tile is TM elements = 32 threads' vectors), so the loads
+// for k-tile kt + 3 are in flight while k-tile kt is computed.
 template <typename T, int H>
 __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* __restrict__ B, int64_t lda,
                                               int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
                                               SimtSmem<T, H>& sm, T (&acc)[2 * H][2 * H]) {
   using V = typename VecT<T, H>::V;
-  constexpr int TM = 32 * H, TK = 8, R = 2 * H;
+  constexpr int TM = 32 * H, TK = 8, R = 2 * H, S = SIMT_STAGES;
+  constexpr int VB = static_cast<int>(sizeof(V));   // bytes each thread copies per operand and k-tile
   const int tid = threadIdx.x;
   const int lrow = tid / (TM / H), lcol = (tid % (TM / H)) * H;
   const T* Ag = A + lrow * lda + m0 + lcol;
   const T* Bg = B + lrow * ldb + n0 + lcol;
-  V ra = __ldg(reinterpret_cast<const V*>(Ag));
-  V rb = __ldg(reinterpret_cast<const V*>(Bg));
-  *reinterpret_cast<V*>(&sm.As[0][lrow][lcol]) = ra;
-  *reinterpret_cast<V*>(&sm.Bs[0][lrow][lcol]) = rb;
-  __syncthreads();
+  const int64_t nk = Kp / TK;
+  // prologue: k-tiles 0 .. S-2
+#pragma unroll
+  for (int st = 0; st < S - 1; ++st) {
+    if (st < nk) {
+      cp_async<VB>(&sm.As[st][lrow][lcol], Ag + st * TK * lda);
+      cp_async<VB>(&sm.Bs[st][lrow][lcol], Bg + st * TK * ldb);
+    }
+    cp_async_commit();
+  }
 #pragma unroll
   for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[i][j] = T(0);
   const int tm = tid & 15, tn = tid >> 4;
-  const int64_t nk = Kp / TK;
-  int buf = 0;
   for (int64_t kt = 0; kt < nk; ++kt) {
-    const bool more = (kt + 1 < nk);
-    if (more) {
-      Ag += TK * lda;
-      Bg += TK * ldb;
-      ra = __ldg(reinterpret_cast<const V*>(Ag));
-      rb = __ldg(reinterpret_cast<const V*>(Bg));
+    cp_async_wait<S - 2>();      // k-tile kt has landed (for this thread) ...
+    __syncthreads();             // ... and for every thread; stage (kt-1) % S is free
+    const int64_t nxt = kt + S - 1;
+    if (nxt < nk) {
+      const int st = static_cast<int>(nxt % S);
+      cp_async<VB>(&sm.As[st][lrow][lcol], Ag + nxt * TK * lda);
+      cp_async<VB>(&sm.Bs[st][lrow][lcol], Bg + nxt * TK * ldb);
     }
+    cp_async_commit();
+    const int buf = static_cast<int>(kt % S);
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
       T a[R], b[R];
@@ -86,13 +114,8 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
-    if (more) {
-      *reinterpret_cast<V*>(&sm.As[buf ^ 1][lrow][lcol]) = ra;
-      *reinterpret_cast<V*>(&sm.Bs[buf ^ 1][lrow][lcol]) = rb;
-      __syncthreads();
-      buf ^= 1;
-    }
   }
+  cp_async_wait<0>();
 }
 
 template <typename T, int H, int CDT, int MODE>
