@@ -27,6 +27,9 @@
  *       C complex: C_new = beta * C + alpha * P
  *     Imaginary alpha is an error in cases 1a, 1b, 1c, 2ab, 2ac, 2bc (Sec. 7.2); in
  *     case 0 it is dropped (projected), in case 3 it is honoured.
+ *     With literal_alpha set, the "literal interpretation" that Sec. 7.2 describes is
+ *     taken instead: every operand's domain at face value, so no case rejects a
+ *     complex alpha and, with C real, C_new = Re(beta) * C + Re(alpha * P).
  *     beta == 0 means C is not read, and alpha == 0 (after its cast) means A and B
  *     are not read (BLAS conventions; the paper is silent on both).
  *  4. The length-k sums use the compensated dot product Dot2 of Ogita, Rump and
@@ -122,13 +125,13 @@ int oracle_mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,
                   const void* B, int dtB, int64_t rsB, int64_t csB,
                   double beta_re, double beta_im,
                   void* C, int dtC, int64_t rsC, int64_t csC,
-                  int comp, double* c_exact, int nthreads) {
+                  int comp, double* c_exact, int nthreads, int literal_alpha) {
     if (transa < 0 || transa > 3 || transb < 0 || transb > 3) return 1;
     if (dtA < 0 || dtA > 3 || dtB < 0 || dtB > 3 || dtC < 0 || dtC > 3) return 1;
     if (comp < 0 || comp > 2 || m < 0 || n < 0 || k < 0) return 1;
     {
         int cse = oracle_case_of(dtC, dtA, dtB);
-        if (alpha_im != 0.0 && cse != 0 && cse != 7) return 2;  /* Sec. 7.2 */
+        if (!literal_alpha && alpha_im != 0.0 && cse != 0 && cse != 7) return 2;  /* Sec. 7.2 */
     }
     if (comp == 2) comp = dt_is_double(dtC) ? 1 : 0;           /* Sec. 5.1.1 */
     {
@@ -166,9 +169,11 @@ int oracle_mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,
                 if (!beta_zero) c = load_elem(C, dtC, i * rsC + j * csC);
                 dot2_init(&out_re); dot2_init(&out_im);
                 if (!c_cplx) {
-                    /* C real: project beta and alpha, keep Re(P) (cases 0, 1a, 1b, 2ab). */
+                    /* C real: project beta and alpha, keep Re(P) (cases 0, 1a, 1b, 2ab);
+                     * literally, Re(alpha * P). */
                     if (!beta_zero) dot2_add(&out_re, br, c.re);
                     dot2_add(&out_re, ar, Pre);
+                    if (literal_alpha) dot2_add(&out_re, -ai, Pim);
                     cn.re = dot2_result(&out_re);
                     cn.im = 0.0;
                 } else {

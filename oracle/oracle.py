@@ -56,7 +56,7 @@ def _load():
             lib.oracle_mxgemm.restype = i32
             lib.oracle_mxgemm.argtypes = [i32, i32, i64, i64, i64, dbl, dbl,
                                           vp, i32, i64, i64, vp, i32, i64, i64,
-                                          dbl, dbl, vp, i32, i64, i64, i32, vp, i32]
+                                          dbl, dbl, vp, i32, i64, i64, i32, vp, i32, i32]
             lib.oracle_case_of.restype = i32
             lib.oracle_case_of.argtypes = [i32, i32, i32]
             _lib = lib
@@ -82,7 +82,7 @@ def oracle_case_of(dtc, dta, dtb):
     return _load().oracle_case_of(DT_CODES[dtc], DT_CODES[dta], DT_CODES[dtb])
 
 
-def oracle_mxgemm(transa, transb, alpha, A, B, beta, C, comp="c", nthreads=None):
+def oracle_mxgemm(transa, transb, alpha, A, B, beta, C, comp="c", nthreads=None, literal_alpha=False):
     """C := beta*C + alpha*op(A)*op(B), in place on the numpy array C.
 
     ``transa``/``transb`` in {'n','t','c','h'} ('c' = conjugate without transpose,
@@ -112,7 +112,7 @@ def oracle_mxgemm(transa, transb, alpha, A, B, beta, C, comp="c", nthreads=None)
                                B.ctypes.data, DT_CODES[_dt_of(B)], rsb, csb,
                                be.real, be.imag,
                                C.ctypes.data, DT_CODES[_dt_of(C)], rsc, csc,
-                               compc, out.ctypes.data, int(nthreads))
+                               compc, out.ctypes.data, int(nthreads), 1 if literal_alpha else 0)
     if st != 0:
         raise OracleError(st)
     return out

@@ -363,3 +363,72 @@ def test_alpha_zero_does_not_read_A_and_B():
     C1 = C0.copy(order="F")
     oracle_mxgemm("n", "n", 1e-50, A, B, -0.5, C1, comp="s")   # 1e-50 rounds to 0 in single
     assert np.array_equal(C1, (-0.5 * C0).astype(C0.dtype))
+
+
+# ---------------------------------------------------------------- literal complex alpha
+def frac_literal(combo, transa, transb, alpha, A, B, beta, C):
+    """Sec. 7.2's literal interpretation in exact rationals: all domains at face value,
+    C_new = beta*C + alpha*op(A)*op(B) in complex arithmetic, then projected onto C's
+    domain (Re when C is real)."""
+    dc, da, db, x = combo
+    prec_c = "d" if dc in ("d", "z") else "s"
+    comp = prec_c if x == "c" else x
+    opA, opB = _fr_op(A, transa), _fr_op(B, transb)
+    m, k = len(opA), len(opA[0]) if opA else 0
+    n = len(opB[0]) if opB else 0
+    cast = lambda z: (Fraction(_rnd(float(z[0]), comp)), Fraction(_rnd(float(z[1]), comp)))
+    Ah = [[cast(v) for v in r] for r in opA]
+    Bh = [[cast(v) for v in r] for r in opB]
+    al, be = complex(alpha), complex(beta)
+    ar, ai = Fraction(_rnd(al.real, comp)), Fraction(_rnd(al.imag, comp))
+    br, bi = Fraction(_rnd(be.real, prec_c)), Fraction(_rnd(be.imag, prec_c))
+    if dc not in CPLX:
+        bi = Fraction(0)
+    Cin = [[complex(v) for v in r] for r in np.asarray(C).tolist()]
+    res = []
+    for i in range(m):
+        row = []
+        for j in range(n):
+            pr = sum((Ah[i][p][0] * Bh[p][j][0] - Ah[i][p][1] * Bh[p][j][1] for p in range(k)), Fraction(0))
+            pi = sum((Ah[i][p][0] * Bh[p][j][1] + Ah[i][p][1] * Bh[p][j][0] for p in range(k)), Fraction(0))
+            cr, ci = Fraction(Cin[i][j].real), Fraction(Cin[i][j].imag)
+            re = br * cr - bi * ci + ar * pr - ai * pi
+            im = br * ci + bi * cr + ar * pi + ai * pr
+            row.append((re, Fraction(0) if dc not in CPLX else im))
+        res.append(row)
+    return res
+
+
+@pytest.mark.parametrize("combo", [c for c in synth.all_combos()
+                                   if oracle.oracle_case_of(c[0], c[1], c[2]) not in (0, 7)])
+def test_literal_alpha_bruteforce(combo):
+    """Literal complex alpha in the six mixed cases equals the exact face-value result."""
+    rng = np.random.default_rng(abs(hash(combo + "lit")) % (2 ** 32))
+    dc, da, db = combo[:3]
+    for ta, tb in (("n", "n"), ("t", "c"), ("h", "t")):
+        m, n, k = (int(v) for v in rng.integers(1, 4, size=3))
+        A = _dyadic(rng, (k, m) if ta in "th" else (m, k), da)
+        B = _dyadic(rng, (n, k) if tb in "th" else (k, n), db)
+        C0 = _dyadic(rng, (m, n), dc)
+        alpha, beta = 0.75 - 1.25j, (0.5 + 0.25j) if dc in CPLX else -0.5
+        Cw = np.asfortranarray(C0.copy())
+        out = oracle_mxgemm(ta, tb, alpha, A, B, beta, Cw, comp=combo[3], literal_alpha=True)
+        exp = frac_literal(combo, ta, tb, alpha, A, B, beta, C0)
+        for i in range(m):
+            for j in range(n):
+                assert out[i, j].real == float(exp[i][j][0]) and out[i, j].imag == float(exp[i][j][1]), \
+                    (combo, ta, tb, i, j)
+    # without the flag the same call is the paper's error
+    with pytest.raises(OracleError):
+        oracle_mxgemm("n", "n", 1j, synth.matrix(rng, 2, 2, da), synth.matrix(rng, 2, 2, db), 1.0,
+                      synth.matrix(rng, 2, 2, dc), comp=combo[3])
+
+
+def test_literal_alpha_agrees_with_paper_rule_for_real_alpha():
+    """For real alpha the literal reading and the paper's rule coincide."""
+    for combo in ("dzdd", "sszs", "dczd", "zsds", "zzsd", "cdzs"):
+        A, B, C0 = synth.problem(31, combo, 7, 6, 5)
+        C1, C2 = C0.copy(order="F"), C0.copy(order="F")
+        r1 = oracle_mxgemm("n", "n", -1.5, A, B, 0.5, C1, comp=combo[3])
+        r2 = oracle_mxgemm("n", "n", -1.5, A, B, 0.5, C2, comp=combo[3], literal_alpha=True)
+        assert np.array_equal(r1, r2)
