@@ -647,9 +647,22 @@ def run_single(args):
     stream = torch.cuda.current_stream()
     combo, n = args.combo, args.size
     gen = torch.Generator(device=dev); gen.manual_seed(3)
-    A = synth.torch_matrix(gen, n, n, combo[1], dev)
-    B = synth.torch_matrix(gen, n, n, combo[2], dev)
-    C = synth.torch_matrix(gen, n, n, combo[0], dev)
+
+    def operand(dt, layout):
+        X = synth.torch_matrix(gen, n, n, dt, dev)            # column-major
+        if layout == "row":
+            return X.contiguous()                             # row-major copy
+        if layout == "gen":                                   # general storage: stride 2 in both
+            big = torch.zeros((2 * n, 2 * n), dtype=X.dtype, device=dev)
+            v = big[::2, ::2]
+            v.copy_(X)
+            return v
+        return X
+
+    la, lb, lc = (args.layout.split(",") + ["col"] * 3)[:3]
+    A = operand(combo[1], la)
+    B = operand(combo[2], lb)
+    C = operand(combo[0], lc)
     h = mx.Handle(); h.set_stream(stream)
     R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
     times = []
@@ -657,7 +670,7 @@ def run_single(args):
     for i in range(args.warmup + args.reps):
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mx.mxgemm_ex(h, args.method, "n", "n", 1.0, A, B, 1.0, C, comp=combo[3])
+        mx.mxgemm_ex(h, args.method, args.transa, args.transb, 1.0, A, B, 1.0, C, comp=combo[3])
         e1.record(stream)
         torch.cuda.synchronize()
         if i == args.warmup - 1 or (args.warmup == 0 and i == 0):
@@ -667,6 +680,7 @@ def run_single(args):
     pack_ms, con_ms, nl = h.phase_times()
     fl = 2.0 * n ** 3 * R
     line = {"workload": "single", "combo": combo, "method": args.method, "n": n, "reps": args.reps,
+            "layout": [la, lb, lc], "trans": [args.transa, args.transb],
             "best_ms": min(times), "gflops": fl / min(times) / 1e6,
             "contraction_ms_mean": con_ms / max(nl, 1), "pack_ms_mean": pack_ms / max(nl, 1),
             "contraction_tflops": fl / (con_ms / max(nl, 1)) / 1e9 if nl else None}
@@ -688,6 +702,9 @@ def main():
     ap.add_argument("--count", type=int, default=2048)
     ap.add_argument("--combo", default="dddd")
     ap.add_argument("--method", default="auto")
+    ap.add_argument("--layout", default="col,col,col", help="storage of A,B,C: col | row | gen")
+    ap.add_argument("--transa", default="n")
+    ap.add_argument("--transb", default="n")
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--streams", type=int, default=4)

@@ -162,6 +162,17 @@ int mxg_plan(int method, int transa, int transb, int64_t m, int64_t n, int64_t k
 int mxg_create(mxg_handle* h);
 int mxg_destroy(mxg_handle h);
 
+/* Literal complex alpha on h (off by default). Sec. 7.2 rejects a non-zero Im(alpha) in
+ * cases 1a, 1b, 1c, 2ab, 2ac and 2bc and names the alternative, a literal
+ * interpretation in which all five operands' domains are taken at face value. With
+ * on != 0, calls on h take that reading: C := beta*C + alpha*op(A)*op(B) in complex
+ * arithmetic, projected onto C's domain (C real: C := Re(beta) C + Re(alpha AB)).
+ * With C real, alpha is folded into the pack of the complex operand (the "special
+ * packing function" for Re(alpha A) of the paper's footnote); with C complex the
+ * epilogue applies the complex alpha. Grouped launches and the server keep the
+ * paper's rule. */
+int mxg_set_literal_alpha(mxg_handle h, int on);
+
 /* Stream for subsequent calls on h (a cudaStream_t; NULL = legacy default stream). */
 int mxg_set_stream(mxg_handle h, void* stream);
 

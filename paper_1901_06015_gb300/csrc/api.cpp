@@ -81,8 +81,9 @@ int make_plan(const Call& c, int method, Plan* p) {
   P = Plan();
   P.call = c;
   P.domain_case = (is_cplx(c.dtC) << 2) | (is_cplx(c.dtA) << 1) | (is_cplx(c.dtB) ? 1 : 0);
-  // Sec. 7.2: non-zero Im(alpha) is an error outside cases 0 and 3.
-  if (c.alpha_im != 0.0 && P.domain_case != MXG_CASE_0 && P.domain_case != MXG_CASE_3)
+  // Sec. 7.2: non-zero Im(alpha) is an error outside cases 0 and 3 (unless the caller
+  // asked for the literal reading, which takes every operand's domain at face value).
+  if (!c.literal_alpha && c.alpha_im != 0.0 && P.domain_case != MXG_CASE_0 && P.domain_case != MXG_CASE_3)
     return MXG_ECOMPLEX_ALPHA;
   // Sec. 5.1.1: the computation precision defaults to C's storage precision.
   P.comp_double = (c.comp == MXG_PREC_OF_C) ? is_dbl(c.dtC) : (c.comp == MXG_PREC_D);
@@ -95,7 +96,8 @@ int make_plan(const Call& c, int method, Plan* p) {
 
   // Sec. 7.1: alpha in the computation precision, beta in C's storage precision.
   P.ar = rnd(c.alpha_re, P.comp_double);
-  P.ai = (P.domain_case == MXG_CASE_3) ? rnd(c.alpha_im, P.comp_double) : 0.0;  // case 0 projects
+  P.ai = (P.domain_case == MXG_CASE_3 || (c.literal_alpha && P.domain_case != MXG_CASE_0))
+             ? rnd(c.alpha_im, P.comp_double) : 0.0;                            // case 0 projects
   P.br = rnd(c.beta_re, is_dbl(c.dtC));
   P.bi = is_cplx(c.dtC) ? rnd(c.beta_im, is_dbl(c.dtC)) : 0.0;                   // real C projects
   P.beta_zero = (P.br == 0.0 && P.bi == 0.0);
@@ -135,6 +137,11 @@ int make_plan(const Call& c, int method, Plan* p) {
       pa = PAT_ONE_E; pb = PAT_SPLIT_K; mode = OUT_ROWPAIR; P.real_products = 4; break;
   }
   P.pat_a = pa; P.pat_b = pb; P.mode = mode;
+  // Literal complex alpha with C real (cases 1a, 1b, 2ab): Re(alpha A B) = Re((alpha A) B),
+  // so alpha is folded into the pack of a complex operand and the epilogue uses 1.
+  if (c.literal_alpha && P.ai != 0.0 && !is_cplx(w.dtC)) {
+    if (is_cplx(w.dtA)) P.fold_a = 1; else P.fold_b = 1;
+  }
   P.conj_a = is_conj(w.transa) ? 1 : 0;
   P.conj_b = (is_conj(w.transb) ? 1 : 0) ^ conj_b_extra;
   P.Mr = w.m * pat_fm(pa);
@@ -175,6 +182,7 @@ EpiArgs plan_epilogue(const Plan& P) {
   const Call& w = (P.kind == PLAN_GEMM) ? P.work : P.call;
   e.C = w.C; e.rs = w.rsC; e.cs = w.csC; e.m = w.m; e.n = w.n;
   e.ar = P.ar; e.ai = P.ai; e.br = P.br; e.bi = P.bi; e.beta_zero = P.beta_zero;
+  if (P.fold_a || P.fold_b) { e.ar = 1.0; e.ai = 0.0; }   // alpha already applied by the pack
   return e;
 }
 
@@ -193,6 +201,7 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   pa.MN = w.m; pa.K = w.k; pa.pattern = P.pat_a; pa.conj = P.conj_a;
   pa.dst = base; pa.dst_lo = nullptr; pa.ld = P.Mp; pa.MNp = P.Mp; pa.Kp = P.Kp;
   pa.layout = LAYOUT_MN_MAJOR; pa.split = SPLIT_NONE;
+  pa.fold = P.fold_a; pa.fold_re = P.ar; pa.fold_im = P.ai;
   if (P.split != SPLIT_NONE) {
     pa.dst_lo = base + P.plane_a; pa.ld = P.Kp; pa.layout = LAYOUT_K_MAJOR; pa.split = P.split;
   }
@@ -204,6 +213,7 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   pb.MN = w.n; pb.K = w.k; pb.pattern = P.pat_b; pb.conj = P.conj_b;
   pb.dst = base + P.bytes_a; pb.dst_lo = nullptr; pb.ld = P.Np; pb.MNp = P.Np; pb.Kp = P.Kp;
   pb.layout = LAYOUT_MN_MAJOR; pb.split = SPLIT_NONE;
+  pb.fold = P.fold_b; pb.fold_re = P.ar; pb.fold_im = P.ai;
   if (P.split != SPLIT_NONE) {
     pb.dst_lo = base + P.bytes_a + P.plane_b; pb.ld = P.Kp; pb.layout = LAYOUT_K_MAJOR; pb.split = P.split;
   }
@@ -344,6 +354,13 @@ int mxg_destroy(mxg_handle h) {
   return MXG_OK;
 }
 
+int mxg_set_literal_alpha(mxg_handle h, int on) {
+  if (!h) return MXG_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->literal_alpha = (on != 0);
+  return MXG_OK;
+}
+
 int mxg_set_stream(mxg_handle h, void* stream) {
   if (!h) return MXG_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
@@ -439,6 +456,7 @@ int mxgemm_ex(mxg_handle h, int method, int transa, int transb, int64_t m, int64
   c.A = A; c.dtA = dtA; c.rsA = rsA; c.csA = csA;
   c.B = B; c.dtB = dtB; c.rsB = rsB; c.csB = csB;
   c.C = C; c.dtC = dtC; c.rsC = rsC; c.csC = csC; c.comp = comp_prec;
+  c.literal_alpha = h->literal_alpha ? 1 : 0;
   Plan P;
   int st = make_plan(c, method, &P);
   if (st != MXG_OK) return st;

@@ -14,6 +14,7 @@ struct mxg_context {
   bool ws_owned = true;
   int* dev_err = nullptr;
   bool timing = false;
+  bool literal_alpha = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<cudaEvent_t> ev_rec;   // triples: before packs, before contraction, after
   std::mutex mu;

@@ -40,9 +40,10 @@ __device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j
     c[0] = e.beta_zero ? t : add_rn(mul_rn(static_cast<CT>(e.br), c[0]), t);
   } else {
     AccT tr, ti;
+    const AccT ai_ = static_cast<AccT>(e.ai);
     if constexpr (MODE == OUT_RE_ONLY) {
-      tr = mul_rn(ar, pr);     // case 1c: alpha is real; the product reaches Re(C) only
-      ti = AccT(0);
+      tr = mul_rn(ar, pr);     // case 1c: the product is real; with a real alpha it reaches Re(C) only
+      ti = mul_rn(ai_, pr);    // (a complex alpha only under the literal reading)
     } else {
       const AccT ai = static_cast<AccT>(e.ai);
       tr = sub_rn(mul_rn(ar, pr), mul_rn(ai, pi));  // complex alpha honoured (case 3)
@@ -51,14 +52,14 @@ __device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j
     const CT tcr = static_cast<CT>(tr), tci = static_cast<CT>(ti);
     if (e.beta_zero) {
       c[0] = tcr;
-      c[1] = tci;
+      c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? CT(0) : tci;
     } else {
       const CT br = static_cast<CT>(e.br), bi = static_cast<CT>(e.bi);
       const CT cr = c[0], ci = c[1];
       const CT bcr = sub_rn(mul_rn(br, cr), mul_rn(bi, ci));
       const CT bci = add_rn(mul_rn(br, ci), mul_rn(bi, cr));
       c[0] = add_rn(bcr, tcr);
-      c[1] = (MODE == OUT_RE_ONLY) ? bci : add_rn(bci, tci);
+      c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? bci : add_rn(bci, tci);
     }
   }
 }

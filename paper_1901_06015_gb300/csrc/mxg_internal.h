@@ -58,6 +58,8 @@ struct PackArgs {
   int64_t MNp, Kp;   // padded extent of the packed operand (written in full, zero padding)
   int layout;        // PackLayout
   int split;         // SplitKind
+  int fold;          // multiply each element by (fold_re + i fold_im) before the pattern
+  double fold_re, fold_im;
 };
 
 struct EpiArgs {

@@ -35,6 +35,20 @@ __device__ __forceinline__ float tf32_rne(float x) {
   return __uint_as_float(u);
 }
 
+// a*b - c*d and a*b + c*d with each product and the sum rounded (no FMA contraction)
+__device__ __forceinline__ float mul_sub(float a, float b, float c, float d) {
+  return __fsub_rn(__fmul_rn(a, b), __fmul_rn(c, d));
+}
+__device__ __forceinline__ double mul_sub(double a, double b, double c, double d) {
+  return __dsub_rn(__dmul_rn(a, b), __dmul_rn(c, d));
+}
+__device__ __forceinline__ float mul_add(float a, float b, float c, float d) {
+  return __fadd_rn(__fmul_rn(a, b), __fmul_rn(c, d));
+}
+__device__ __forceinline__ double mul_add(double a, double b, double c, double d) {
+  return __dadd_rn(__dmul_rn(a, b), __dmul_rn(c, d));
+}
+
 template <typename DT>
 __device__ __forceinline__ DT pattern_value(int pattern, int s, int t, DT xr, DT xi) {
   // (for a real source the planner only uses PAT_RE, so xi is never read there)
@@ -95,11 +109,19 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    sm.re[lp_[i]][lm_[i]] = static_cast<DT>(vr_[i]);
+    DT re = static_cast<DT>(vr_[i]);
     if constexpr (SC) {   // a real source only ever uses the RE pattern
-      const DT im = static_cast<DT>(vi_[i]);
-      sm.im[lp_[i]][lm_[i]] = a.conj ? -im : im;
+      DT im = static_cast<DT>(vi_[i]);
+      if (a.conj) im = -im;
+      if (a.fold) {       // alpha * x in the computation precision (literal complex alpha)
+        const DT fr = static_cast<DT>(a.fold_re), fi = static_cast<DT>(a.fold_im);
+        const DT nr = mul_sub(fr, re, fi, im), ni = mul_add(fr, im, fi, re);
+        re = nr;
+        im = ni;
+      }
+      sm.im[lp_[i]][lm_[i]] = im;
     }
+    sm.re[lp_[i]][lm_[i]] = re;
   }
   __syncthreads();
   const int nk_out = PK_P * fk, nm_out = PK_MN * fm;

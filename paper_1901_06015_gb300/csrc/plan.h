@@ -16,6 +16,7 @@ struct Call {
   const void* B; int dtB; int64_t rsB, csB;
   void* C; int dtC; int64_t rsC, csC;
   int comp;
+  int literal_alpha;   // Sec. 7.2's literal reading: complex alpha honoured in every case
 };
 
 enum PlanKind : int { PLAN_NOOP = 0, PLAN_SCALE = 1, PLAN_GEMM = 2 };
@@ -32,6 +33,7 @@ struct Plan {
   bool beta_zero = false, alpha_zero = false;
   int pat_a = PAT_RE, pat_b = PAT_RE, mode = OUT_REAL;
   int conj_a = 0, conj_b = 0;
+  int fold_a = 0, fold_b = 0;       // alpha folded into this operand's pack (literal alpha, C real)
   int real_products = 1;
   int64_t Mr = 0, Nr = 0, Kr = 0;   // real gemm
   int64_t Mp = 0, Np = 0, Kp = 0;   // padded to the kernel's tiles

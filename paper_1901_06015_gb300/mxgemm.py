@@ -80,6 +80,8 @@ def lib():
             L.mxg_create.argtypes = [ctypes.POINTER(_vp)]
             L.mxg_destroy.restype = _i32
             L.mxg_destroy.argtypes = [_vp]
+            L.mxg_set_literal_alpha.restype = _i32
+            L.mxg_set_literal_alpha.argtypes = [_vp, _i32]
             L.mxg_set_stream.restype = _i32
             L.mxg_set_stream.argtypes = [_vp, _vp]
             L.mxg_set_workspace.restype = _i32
@@ -190,6 +192,12 @@ class Handle:
             raise MxgError(st, "mxg_create")
         self.h = h
         self._ws = None
+
+    def set_literal_alpha(self, on):
+        """Sec. 7.2's literal reading of a complex alpha for calls on this handle."""
+        st = lib().mxg_set_literal_alpha(self.h, 1 if on else 0)
+        if st:
+            raise MxgError(st, "mxg_set_literal_alpha")
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""

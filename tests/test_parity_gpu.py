@@ -157,3 +157,34 @@ def test_bounded_device_wait_reports_timeout_and_context_survives():
     A, B, C0 = synth.problem(13, "ssss", 64, 64, 64)
     _check("ssss", A, B, C0, 1.0, 0.0, method="bf16x3")
     h.close()
+
+
+MIXED = [c for c in REPS if c[:3] not in ("sss", "ssd", "sds", "sdd", "dss", "dsd", "dds", "ddd")
+         and not all(x in "cz" for x in c[:3])]
+
+
+@pytest.mark.parametrize("combo", MIXED)
+def test_literal_complex_alpha(combo):
+    """Sec. 7.2's literal reading (handle option): a complex alpha in the six mixed
+    cases, against the oracle's literal mode, for every method, row- and column-stored
+    C (the whole-operation transpose moves alpha's fold to the other operand)."""
+    import paper_1901_06015_gb300 as mx
+    h = mx.Handle()
+    h.set_stream(torch.cuda.current_stream())
+    h.set_literal_alpha(True)
+    alpha, beta = 0.75 - 1.25j, (0.5 + 0.25j) if combo[0] in "cz" else -0.5
+    for order_c in "FC":
+        A, B, C0 = synth.problem(17, combo, 70, 45, 90, order_c=order_c)
+        ref_C = np.array(C0, order="K")
+        ref = oracle_mxgemm("n", "n", alpha, A, B, beta, ref_C, comp=combo[3], literal_alpha=True)
+        for meth in methods_for(combo):
+            dA, dB, dC = to_device(A), to_device(B), to_device(C0)
+            mx.mxgemm_ex(h, meth, "n", "n", alpha, dA, dB, beta, dC, comp=combo[3])
+            torch.cuda.synchronize()
+            err, _ = normwise_error(combo, dC.cpu().numpy(), ref, A, B, C0, alpha, beta)
+            assert err <= tolerance(combo, 90, meth), (combo, meth, order_c, err)
+    # the same call on a default handle is the paper's error
+    with pytest.raises(mx.MxgError) as e:
+        mx.mxgemm_ex(None, "auto", "n", "n", alpha, to_device(A), to_device(B), beta, to_device(C0), comp=combo[3])
+    assert e.value.status == 2
+    h.close()
