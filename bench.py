@@ -646,24 +646,26 @@ def run_single(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     combo, n = args.combo, args.size
+    mm, nn, kk = (int(x) for x in args.mnk.split(",")) if args.mnk else (n, n, n)
     gen = torch.Generator(device=dev); gen.manual_seed(3)
 
-    def operand(dt, layout):
-        X = synth.torch_matrix(gen, n, n, dt, dev)            # column-major
+    def operand(dt, layout, rows, cols):
+        X = synth.torch_matrix(gen, rows, cols, dt, dev)      # column-major
         if layout == "row":
             return X.contiguous()                             # row-major copy
         if layout == "gen":                                   # general storage: stride 2 in both
-            big = torch.zeros((2 * n, 2 * n), dtype=X.dtype, device=dev)
+            big = torch.zeros((2 * rows, 2 * cols), dtype=X.dtype, device=dev)
             v = big[::2, ::2]
             v.copy_(X)
             return v
         return X
 
     la, lb, lc = (args.layout.split(",") + ["col"] * 3)[:3]
-    A = operand(combo[1], la)
-    B = operand(combo[2], lb)
-    C = operand(combo[0], lc)
+    A = operand(combo[1], la, *((kk, mm) if args.transa in "th" else (mm, kk)))
+    B = operand(combo[2], lb, *((nn, kk) if args.transb in "th" else (kk, nn)))
+    C = operand(combo[0], lc, mm, nn)
     h = mx.Handle(); h.set_stream(stream)
+    h.set_split_k(args.split_k)
     R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
     times = []
     h.set_phase_timing(True)
@@ -678,8 +680,9 @@ def run_single(args):
         if i >= args.warmup:
             times.append(e0.elapsed_time(e1))
     pack_ms, con_ms, nl = h.phase_times()
-    fl = 2.0 * n ** 3 * R
-    line = {"workload": "single", "combo": combo, "method": args.method, "n": n, "reps": args.reps,
+    fl = 2.0 * mm * nn * kk * R
+    line = {"workload": "single", "combo": combo, "method": args.method, "m_n_k": [mm, nn, kk], "reps": args.reps,
+            "split_k": args.split_k,
             "layout": [la, lb, lc], "trans": [args.transa, args.transb],
             "best_ms": min(times), "gflops": fl / min(times) / 1e6,
             "contraction_ms_mean": con_ms / max(nl, 1), "pack_ms_mean": pack_ms / max(nl, 1),
@@ -705,6 +708,8 @@ def main():
     ap.add_argument("--layout", default="col,col,col", help="storage of A,B,C: col | row | gen")
     ap.add_argument("--transa", default="n")
     ap.add_argument("--transb", default="n")
+    ap.add_argument("--mnk", default="", help="m,n,k for --workload single (default: --size cubed)")
+    ap.add_argument("--split-k", type=int, default=0)
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--streams", type=int, default=4)

@@ -110,7 +110,8 @@ typedef struct {
   int64_t Mr, Nr, Kr;       /* dimensions of the real product (M', N', K') */
   int real_products;        /* R = M'N'K' / (mnk): 1, 2 or 4 (flops = 2mnk R) */
   double flops;             /* useful flops 2*m*n*k*R (Fig. "mixeddom") */
-  size_t workspace_bytes;   /* device workspace the call needs (packed operands) */
+  size_t workspace_bytes;   /* device workspace the call needs (packed operands, split-K sums) */
+  int k_splits;             /* split-K slices (1: none; see mxg_set_split_k) */
 } mxg_plan_info;
 
 /*
@@ -172,6 +173,17 @@ int mxg_destroy(mxg_handle h);
  * epilogue applies the complex alpha. Grouped launches and the server keep the
  * paper's rule. */
 int mxg_set_literal_alpha(mxg_handle h, int on);
+
+/* Split-K on h (off by default): the paper's C_temp in the computation precision
+ * (Secs. 6.2-6.4) used for parallelism over K. K' is cut into slices computed by
+ * separate CTAs into a workspace of partial sums (splits x M' x N' in the computation
+ * precision); a reduction adds the slices in a fixed order and applies the epilogue
+ * once, so results are deterministic but round differently from the unsplit call.
+ * mode: 0 off; 1 automatic (split only when the tile grid has fewer tiles than the
+ * device has SMs, keeping at least 512 k per slice); n >= 2 exactly n slices (fewer
+ * when K' is short). Applies to the FFMA, DFMA and DMMA methods; the split-precision
+ * tensor-core methods and grouped launches do not split. */
+int mxg_set_split_k(mxg_handle h, int mode);
 
 /* Stream for subsequent calls on h (a cudaStream_t; NULL = legacy default stream). */
 int mxg_set_stream(mxg_handle h, void* stream);

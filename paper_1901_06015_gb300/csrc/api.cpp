@@ -64,6 +64,8 @@ static bool no_self_overlap(int64_t m, int64_t n, int64_t rs, int64_t cs) {
   return s1 >= 1 && s1 * (e1 - 1) < s2;
 }
 
+static size_t esz_of(const Plan& P) { return P.comp_double ? 8 : 4; }
+
 int make_plan(const Call& c, int method, Plan* p) {
   if (!trans_ok(c.transa) || !trans_ok(c.transb)) return MXG_EINVAL;
   if (!dt_ok(c.dtA) || !dt_ok(c.dtB) || !dt_ok(c.dtC)) return MXG_EINVAL;
@@ -164,7 +166,26 @@ int make_plan(const Call& c, int method, Plan* p) {
     P.bytes_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
     P.bytes_b = align256(static_cast<size_t>(P.Kp) * P.Np * esz);
   }
-  P.workspace = P.bytes_a + P.bytes_b;
+  // Split-K (Secs. 6.2-6.4: a workspace in the computation precision), only on request.
+  if (c.split_k && P.split == SPLIT_NONE) {
+    const int64_t tiles = (P.Mp / t.tm) * (P.Np / t.tn);
+    const int64_t ktiles = P.Kp / t.tk;
+    const int64_t min_ktiles = std::max<int64_t>(1, 512 / t.tk);   // at least 512 k per slice
+    int64_t S = c.split_k;
+    if (c.split_k == 1) {
+      const int64_t sms = c.sm_count > 0 ? c.sm_count : 152;
+      S = tiles >= sms ? 1 : (2 * sms + tiles - 1) / tiles;
+      S = std::min<int64_t>(S, std::max<int64_t>(1, ktiles / min_ktiles));
+    }
+    S = std::max<int64_t>(1, std::min<int64_t>({S, ktiles, 65535}));
+    if (S > 1) {
+      const int64_t per = (ktiles + S - 1) / S;       // k-tiles per slice
+      P.kslice = per * t.tk;
+      P.splits = static_cast<int>((P.Kp + P.kslice - 1) / P.kslice);
+      P.bytes_ws = align256(static_cast<size_t>(P.splits) * P.Mp * P.Np * esz_of(P));
+    }
+  }
+  P.workspace = P.bytes_a + P.bytes_b + P.bytes_ws;
   return MXG_OK;
 }
 
@@ -229,6 +250,9 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   GemmArgs g;
   g.A = base; g.B = base + P.bytes_a; g.lda = P.Mp; g.ldb = P.Np; g.Kp = P.Kp;
   g.Mp = P.Mp; g.Np = P.Np; g.e = plan_epilogue(P);
+  if (P.splits > 1)
+    return cuda_status(launch_gemm_splitk(P.method, w.dtC, P.mode, g, P.splits, P.kslice,
+                                          base + P.bytes_a + P.bytes_b, s));
   return cuda_status(launch_gemm_simt(P.method, w.dtC, P.mode, g, s));
 }
 
@@ -323,6 +347,7 @@ int mxg_plan(int method, int transa, int transb, int64_t m, int64_t n, int64_t k
     info->real_products = P.real_products;
     info->flops = 2.0 * static_cast<double>(m) * static_cast<double>(n) * static_cast<double>(k) * P.real_products;
     info->workspace_bytes = P.workspace;
+    info->k_splits = P.splits;
   }
   return MXG_OK;
 }
@@ -332,6 +357,7 @@ int mxg_create(mxg_handle* out) {
   mxg_context* h = new (std::nothrow) mxg_context();
   if (!h) return MXG_ENOMEM;
   cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->dev_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -351,6 +377,13 @@ int mxg_destroy(mxg_handle h) {
   recycle_events(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
+  return MXG_OK;
+}
+
+int mxg_set_split_k(mxg_handle h, int mode) {
+  if (!h || mode < 0 || mode > 65535) return MXG_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->split_k = mode;
   return MXG_OK;
 }
 
@@ -457,6 +490,8 @@ int mxgemm_ex(mxg_handle h, int method, int transa, int transb, int64_t m, int64
   c.B = B; c.dtB = dtB; c.rsB = rsB; c.csB = csB;
   c.C = C; c.dtC = dtC; c.rsC = rsC; c.csC = csC; c.comp = comp_prec;
   c.literal_alpha = h->literal_alpha ? 1 : 0;
+  c.split_k = h->split_k;
+  c.sm_count = h->sm_count;
   Plan P;
   int st = make_plan(c, method, &P);
   if (st != MXG_OK) return st;

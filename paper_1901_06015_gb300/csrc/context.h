@@ -15,6 +15,8 @@ struct mxg_context {
   int* dev_err = nullptr;
   bool timing = false;
   bool literal_alpha = false;
+  int split_k = 0;
+  int sm_count = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<cudaEvent_t> ev_rec;   // triples: before packs, before contraction, after
   std::mutex mu;

@@ -158,7 +158,30 @@ dmma_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restri
   }
 }
 
+// Split-K slice: k-tiles [z*kslice, ...) of one tile; raw sums to ws[z] (column-major,
+// leading dimension Mp), written through the shared staging tile so stores coalesce.
+__global__ void __launch_bounds__(128) dmma_gemm_partial(GemmArgs g, int64_t kslice, double* __restrict__ ws) {
+  __shared__ __align__(16) double smem[DM_SMEM];
+  double acc[4][4][2];
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * DM_T, n0 = static_cast<int64_t>(blockIdx.y) * DM_T;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * kslice;
+  const int64_t klen = (g.Kp - k0 < kslice) ? g.Kp - k0 : kslice;
+  dmma_mainloop(static_cast<const double*>(g.A) + k0 * g.lda, static_cast<const double*>(g.B) + k0 * g.ldb, g.lda,
+                g.ldb, klen, m0, n0, smem, acc);
+  dmma_stage(smem, acc);
+  double* out = ws + static_cast<int64_t>(blockIdx.z) * g.Mp * g.Np;
+  for (int idx = threadIdx.x; idx < DM_T * DM_T; idx += 128) {
+    const int row = idx % DM_T, col = idx / DM_T;
+    out[(n0 + col) * g.Mp + m0 + row] = smem[col * DM_CLD + row];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_dmma_partial(const GemmArgs& g, int64_t kslice, double* ws, dim3 grid, cudaStream_t s) {
+  dmma_gemm_partial<<<grid, 128, 0, s>>>(g, kslice, ws);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dmma(int mode, int cdt, const GemmArgs& g, cudaStream_t s, dim3 grid) {
   switch (cdt * 4 + mode) {

@@ -18,6 +18,8 @@
 // Each kernel exists as a single-problem launch (C datatype and output mode fixed at
 // compile time) and as a grouped persistent launch that walks a device work list of
 // (problem, tile) entries from many problems, dispatching the epilogue per tile.
+#include <algorithm>
+
 #include "epilogue.cuh"
 #include "grouped.h"
 
@@ -187,6 +189,52 @@ simt_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restri
   }
 }
 
+// Split-K (the paper's C_temp in the computation precision, Secs. 6.2-6.4, here for
+// parallelism over K): slice z = blockIdx.z accumulates k-tiles [z*kslice, ...) of one
+// tile and stores the raw sums to ws[z] (column-major, leading dimension Mp); a
+// reduction then adds the slices in order and applies the epilogue once.
+template <typename T, int H>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3))
+simt_gemm_partial(GemmArgs g, int64_t kslice, T* __restrict__ ws) {
+  __shared__ SimtSmem<T, H> sm;
+  T acc[2 * H][2 * H];
+  constexpr int TM = 32 * H;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * TM, n0 = static_cast<int64_t>(blockIdx.y) * TM;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * kslice;
+  const int64_t klen = (g.Kp - k0 < kslice) ? g.Kp - k0 : kslice;
+  simt_mainloop<T, H>(static_cast<const T*>(g.A) + k0 * g.lda, static_cast<const T*>(g.B) + k0 * g.ldb, g.lda, g.ldb,
+                      klen, m0, n0, sm, acc);
+  T* out = ws + static_cast<int64_t>(blockIdx.z) * g.Mp * g.Np;
+  const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 2 * H; ++i)
+#pragma unroll
+    for (int j = 0; j < 2 * H; ++j) {
+      const int64_t row = m0 + (i < H ? tm * H + i : TM / 2 + tm * H + (i - H));
+      const int64_t col = n0 + (j < H ? tn * H + j : TM / 2 + tn * H + (j - H));
+      out[col * g.Mp + row] = acc[i][j];
+    }
+}
+
+template <typename T, int CDT, int MODE>
+__global__ void splitk_reduce(const T* __restrict__ ws, int splits, int64_t Mp, int64_t Np, EpiArgs e) {
+  const int64_t total = e.m * e.n, slice = Mp * Np;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx % e.m, j = idx / e.m;
+    int64_t o_r, o_i = -1;   // offsets of the real and (paired) imaginary values of P
+    if constexpr (MODE == OUT_ROWPAIR) { o_r = j * Mp + 2 * i; o_i = o_r + 1; }
+    else if constexpr (MODE == OUT_COLPAIR) { o_r = 2 * j * Mp + i; o_i = o_r + Mp; }
+    else { o_r = j * Mp + i; }
+    T pr = ws[o_r], pi = (o_i >= 0) ? ws[o_i] : T(0);
+    for (int z = 1; z < splits; ++z) {
+      pr = add_rn(pr, ws[z * slice + o_r]);
+      if (o_i >= 0) pi = add_rn(pi, ws[z * slice + o_i]);
+    }
+    epi_store<T, CDT, MODE>(e, i, j, pr, pi);
+  }
+}
+
 // C := beta * C (k == 0 or alpha == 0: A and B are not read).
 template <int CDT>
 __global__ void scale_c_kernel(EpiArgs e) {
@@ -261,6 +309,50 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
     case MXG_D: return launch_for_c<MXG_D>(method, mode, g, s);
     case MXG_C: return launch_for_c<MXG_C>(method, mode, g, s);
     case MXG_Z: return launch_for_c<MXG_Z>(method, mode, g, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t launch_reduce(int c_dt, int mode, const T* ws, int splits, int64_t Mp, int64_t Np, const EpiArgs& e,
+                          cudaStream_t s) {
+  const int64_t total = e.m * e.n;
+  if (total <= 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+  switch (c_dt * 4 + mode) {
+    case MXG_S * 4 + OUT_REAL: splitk_reduce<T, MXG_S, OUT_REAL><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_D * 4 + OUT_REAL: splitk_reduce<T, MXG_D, OUT_REAL><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_C * 4 + OUT_RE_ONLY: splitk_reduce<T, MXG_C, OUT_RE_ONLY><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_C * 4 + OUT_ROWPAIR: splitk_reduce<T, MXG_C, OUT_ROWPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_C * 4 + OUT_COLPAIR: splitk_reduce<T, MXG_C, OUT_COLPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_Z * 4 + OUT_RE_ONLY: splitk_reduce<T, MXG_Z, OUT_RE_ONLY><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_Z * 4 + OUT_ROWPAIR: splitk_reduce<T, MXG_Z, OUT_ROWPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    case MXG_Z * 4 + OUT_COLPAIR: splitk_reduce<T, MXG_Z, OUT_COLPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_splitk(int method, int c_dt, int mode, const GemmArgs& g, int splits, int64_t kslice,
+                               void* ws, cudaStream_t s) {
+  const TileCfg t = tile_cfg(method);
+  const int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
+  if (gx <= 0 || gy <= 0) return cudaSuccess;
+  if (gx > 0x7fffffffLL || gy > 65535 || splits < 1 || splits > 65535) return cudaErrorInvalidValue;
+  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(splits));
+  cudaError_t e;
+  switch (method) {
+    case MXG_METHOD_FFMA:
+      simt_gemm_partial<float, 4><<<grid, 256, 0, s>>>(g, kslice, static_cast<float*>(ws));
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      return launch_reduce<float>(c_dt, mode, static_cast<const float*>(ws), splits, g.Mp, g.Np, g.e, s);
+    case MXG_METHOD_DFMA:
+      simt_gemm_partial<double, 2><<<grid, 256, 0, s>>>(g, kslice, static_cast<double*>(ws));
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      return launch_reduce<double>(c_dt, mode, static_cast<const double*>(ws), splits, g.Mp, g.Np, g.e, s);
+    case MXG_METHOD_DMMA:
+      if ((e = launch_dmma_partial(g, kslice, static_cast<double*>(ws), grid, s)) != cudaSuccess) return e;
+      return launch_reduce<double>(c_dt, mode, static_cast<const double*>(ws), splits, g.Mp, g.Np, g.e, s);
   }
   return cudaErrorInvalidValue;
 }

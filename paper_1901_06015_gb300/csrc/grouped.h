@@ -51,6 +51,7 @@ cudaError_t launch_dmma(int mode, int cdt, const GemmArgs& g, cudaStream_t s, di
 cudaError_t launch_dmma_grouped(const GroupProb* probs, const GroupTile* tiles, int ntiles, int* counter, int sched,
                                 int grid, cudaStream_t s);
 int dmma_grouped_blocks_per_sm();
+cudaError_t launch_dmma_partial(const GemmArgs& g, int64_t kslice, double* ws, dim3 grid, cudaStream_t s);
 int grouped_blocks_per_sm(int variant);
 cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const GroupTile* tiles, int ntiles,
                                 int* counter, int sched, int grid, cudaStream_t s);

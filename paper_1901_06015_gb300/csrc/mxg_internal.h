@@ -88,6 +88,10 @@ TileCfg tile_cfg(int method);
 cudaError_t launch_pack(const PackArgs& a, int comp_double, cudaStream_t s);
 cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_scale_c(const EpiArgs& e, int c_dt, cudaStream_t s);
+// Split-K: `splits` slices of kslice k elements accumulate into ws (splits x Np x Mp in
+// the computation precision), then an ordered reduction applies the epilogue.
+cudaError_t launch_gemm_splitk(int method, int c_dt, int mode, const GemmArgs& g, int splits, int64_t kslice,
+                               void* ws, cudaStream_t s);
 // Bounded-wait self-test: a wait nothing will satisfy, limited to `seconds`.
 cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s);
 // Split-precision tensor-core contraction: planes = {A_hi, A_lo, B_hi, B_lo}, K-major.

@@ -17,6 +17,8 @@ struct Call {
   void* C; int dtC; int64_t rsC, csC;
   int comp;
   int literal_alpha;   // Sec. 7.2's literal reading: complex alpha honoured in every case
+  int split_k;         // 0 off, 1 automatic, >= 2 that many K slices (SIMT and DMMA methods)
+  int sm_count;        // SMs of the device (0: assume 152) for the automatic split
 };
 
 enum PlanKind : int { PLAN_NOOP = 0, PLAN_SCALE = 1, PLAN_GEMM = 2 };
@@ -39,6 +41,9 @@ struct Plan {
   int64_t Mp = 0, Np = 0, Kp = 0;   // padded to the kernel's tiles
   int split = SPLIT_NONE;           // hi/lo planes for the tensor-core methods
   size_t plane_a = 0, plane_b = 0;  // bytes of one plane (split methods)
+  int splits = 1;                   // split-K slices
+  int64_t kslice = 0;               // k elements per slice
+  size_t bytes_ws = 0;              // split-K partial sums
   size_t bytes_a = 0, bytes_b = 0, workspace = 0;
 };
 

@@ -25,7 +25,7 @@ _lib = None
 class PlanInfo(ctypes.Structure):
     _fields_ = [("domain_case", _i32), ("comp_prec", _i32), ("method", _i32),
                 ("whole_op_transposed", _i32), ("Mr", _i64), ("Nr", _i64), ("Kr", _i64),
-                ("real_products", _i32), ("flops", _dbl), ("workspace_bytes", _sz)]
+                ("real_products", _i32), ("flops", _dbl), ("workspace_bytes", _sz), ("k_splits", _i32)]
 
 
 class Problem(ctypes.Structure):
@@ -80,6 +80,8 @@ def lib():
             L.mxg_create.argtypes = [ctypes.POINTER(_vp)]
             L.mxg_destroy.restype = _i32
             L.mxg_destroy.argtypes = [_vp]
+            L.mxg_set_split_k.restype = _i32
+            L.mxg_set_split_k.argtypes = [_vp, _i32]
             L.mxg_set_literal_alpha.restype = _i32
             L.mxg_set_literal_alpha.argtypes = [_vp, _i32]
             L.mxg_set_stream.restype = _i32
@@ -192,6 +194,12 @@ class Handle:
             raise MxgError(st, "mxg_create")
         self.h = h
         self._ws = None
+
+    def set_split_k(self, mode):
+        """Split-K: 0 off, 1 automatic, n >= 2 slices (see mxg_set_split_k)."""
+        st = lib().mxg_set_split_k(self.h, int(mode))
+        if st:
+            raise MxgError(st, "mxg_set_split_k")
 
     def set_literal_alpha(self, on):
         """Sec. 7.2's literal reading of a complex alpha for calls on this handle."""

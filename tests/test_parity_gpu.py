@@ -188,3 +188,34 @@ def test_literal_complex_alpha(combo):
         mx.mxgemm_ex(None, "auto", "n", "n", alpha, to_device(A), to_device(B), beta, to_device(C0), comp=combo[3])
     assert e.value.status == 2
     h.close()
+
+
+@pytest.mark.parametrize("splits", [2, 3, 7, 1])   # 1 = automatic
+def test_split_k(splits):
+    """Split-K (handle option): skinny problems with long k, every SIMT method, every
+    output mode (real C, Re(C) only, row pairs, column pairs), against the oracle;
+    bit-exact on small integers, where every summation order is exact."""
+    import paper_1901_06015_gb300 as mx
+    h = mx.Handle()
+    h.set_stream(torch.cuda.current_stream())
+    h.set_split_k(splits)
+    for combo in ("dsdd", "sdss", "zddd", "csss", "zzdd", "cccs", "zszd", "cscs", "ddzd"):
+        m, n, k = 70, 50, 4100
+        info = mx.mxg_plan(combo, m, n, k)
+        for dist in ("uniform", "smallint"):
+            A, B, C0 = synth.problem(19, combo, m, n, k, dist=dist)
+            ref_C = C0.copy(order="F")
+            ref = oracle_mxgemm("n", "n", 1.5, A, B, -0.5, ref_C, comp=combo[3])
+            for meth in methods_for(combo):
+                if meth in ("tf32x3", "bf16x3"):
+                    continue
+                dA, dB, dC = to_device(A), to_device(B), to_device(C0)
+                mx.mxgemm_ex(h, meth, "n", "n", 1.5, dA, dB, -0.5, dC, comp=combo[3])
+                torch.cuda.synchronize()
+                got = dC.cpu().numpy()
+                if dist == "smallint":
+                    assert np.array_equal(got, ref_C), (combo, meth, splits)
+                else:
+                    err, _ = normwise_error(combo, got, ref, A, B, C0, 1.5, -0.5)
+                    assert err <= tolerance(combo, k, meth), (combo, meth, splits, err)
+    h.close()
