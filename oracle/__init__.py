@@ -5,5 +5,5 @@ may import this package. The library (``paper_1901_06015_gb300``) never does, an
 this package imports nothing from the library.
 """
 from .oracle import (  # noqa: F401
-    DT_CODES, TRANS_CODES, build, oracle_mxgemm, oracle_case_of, OracleError,
+    DT_CODES, TRANS_CODES, build, oracle_mxgemm, oracle_case_of, oracle_round, OracleError,
 )

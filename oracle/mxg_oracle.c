@@ -39,8 +39,12 @@
  *     overwritten with C_new rounded (RN-even) to C's storage datatype.
  *
  * Datatype codes: 0 = s (real single), 1 = d (real double), 2 = c (complex single),
- * 3 = z (complex double). Trans codes: 0 = N, 1 = T, 2 = conj only, 3 = conj-trans.
- * Computation precision: 0 = single, 1 = double, 2 = that of C.
+ * 3 = z (complex double), 4 = h (real binary16), 5 = k (complex binary16), 6 = b (real
+ * bfloat16), 7 = w (complex bfloat16); a complex element stores (re, im).
+ * Trans codes: 0 = N, 1 = T, 2 = conj only, 3 = conj-trans.
+ * Computation precision: 0 = single, 1 = double, 2 = that of C, 3 = binary16, 4 =
+ * bfloat16 (Sec. 5.3: a further precision; A and B are rounded to it, and, as on the
+ * hardware that computes it, the sums are formed in a wider format -- here exactly).
  * Return: 0 ok, 1 invalid argument, 2 imaginary alpha in a case that forbids it.
  */
 #include <math.h>
@@ -50,8 +54,74 @@
 
 typedef struct { double re, im; } zval;
 
-static int dt_is_complex(int dt) { return dt == 2 || dt == 3; }
-static int dt_is_double(int dt) { return dt == 1 || dt == 3; }
+static int dt_is_complex(int dt) { return dt == 2 || dt == 3 || dt == 5 || dt == 7; }
+/* storage precision of a datatype: 0 single, 1 double, 3 binary16, 4 bfloat16 */
+static int dt_prec(int dt) {
+    switch (dt) {
+    case 1: case 3: return 1;
+    case 4: case 5: return 3;
+    case 6: case 7: return 4;
+    default: return 0;
+    }
+}
+
+/* Round x (binary64) to a binary format with p significant bits, smallest normal
+ * 2^emin and largest finite value (2 - 2^(1-p)) 2^emax: round-to-nearest, ties to
+ * even, gradual underflow, values beyond the largest finite round to infinity (IEEE
+ * 754 semantics written out). Scaling by powers of two is exact, so the quotient and
+ * product below introduce no rounding besides nearbyint's. */
+static double rnd_fmt(double x, int p, int emin, int emax) {
+    double a, q, r, maxv;
+    int e, ex;
+    if (x != x || x == 0.0 || isinf(x)) return x;
+    a = fabs(x);
+    (void)frexp(a, &e);                 /* a in [2^(e-1), 2^e) */
+    ex = e - 1;
+    if (ex < emin) ex = emin;           /* subnormal range: fixed quantum */
+    q = ldexp(1.0, ex - (p - 1));
+    r = nearbyint(a / q) * q;           /* default rounding mode: nearest, ties to even */
+    maxv = ldexp(2.0 - ldexp(1.0, 1 - p), emax);
+    if (r > maxv) r = INFINITY;
+    return copysign(r, x);
+}
+static double rnd_half(double x) { return rnd_fmt(x, 11, -14, 15); }
+static double rnd_bf16(double x) { return rnd_fmt(x, 8, -126, 127); }
+
+/* binary16 bit pattern <-> value */
+static double half_value(uint16_t h) {
+    const int e = (h >> 10) & 31, m = h & 1023;
+    double v;
+    if (e == 0) v = ldexp((double)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexp((double)(m | 1024), e - 25);
+    return (h & 0x8000) ? -v : v;
+}
+static uint16_t half_bits(double x) {   /* x: already a binary16 value, inf or NaN */
+    const uint16_t sgn = signbit(x) ? 0x8000 : 0;
+    const double a = fabs(x);
+    int e, ex;
+    if (a != a) return (uint16_t)(sgn | 0x7e00);
+    if (isinf(a)) return (uint16_t)(sgn | 0x7c00);
+    if (a == 0.0) return sgn;
+    (void)frexp(a, &e);
+    ex = e - 1;
+    if (ex < -14) return (uint16_t)(sgn | (uint16_t)ldexp(a, 24));        /* subnormal: m 2^-24 */
+    return (uint16_t)(sgn | ((ex + 15) << 10) | (uint16_t)((ldexp(a, -ex) - 1.0) * 1024.0));
+}
+/* bfloat16: the upper half of a binary32 pattern */
+static double bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+static uint16_t bf16_bits(double x) {   /* x: already a bfloat16 value, inf or NaN */
+    const float f = (float)x;           /* exact */
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if (x != x) return (uint16_t)((u >> 16) | 0x40);
+    return (uint16_t)(u >> 16);
+}
 
 /* Read element at linear offset off (in elements of dt), widened to complex binary64. */
 static zval load_elem(const void* base, int dt, int64_t off) {
@@ -63,6 +133,12 @@ static zval load_elem(const void* base, int dt, int64_t off) {
             v.im = (double)((const float*)base)[2 * off + 1]; break;
     case 3: v.re = ((const double*)base)[2 * off];
             v.im = ((const double*)base)[2 * off + 1]; break;
+    case 4: v.re = half_value(((const uint16_t*)base)[off]); break;
+    case 5: v.re = half_value(((const uint16_t*)base)[2 * off]);
+            v.im = half_value(((const uint16_t*)base)[2 * off + 1]); break;
+    case 6: v.re = bf16_value(((const uint16_t*)base)[off]); break;
+    case 7: v.re = bf16_value(((const uint16_t*)base)[2 * off]);
+            v.im = bf16_value(((const uint16_t*)base)[2 * off + 1]); break;
     }
     return v;
 }
@@ -75,11 +151,27 @@ static void store_elem(void* base, int dt, int64_t off, zval v) {
             ((float*)base)[2 * off + 1] = (float)v.im; break;
     case 3: ((double*)base)[2 * off] = v.re;
             ((double*)base)[2 * off + 1] = v.im; break;
+    case 4: ((uint16_t*)base)[off] = half_bits(rnd_half(v.re)); break;
+    case 5: ((uint16_t*)base)[2 * off] = half_bits(rnd_half(v.re));
+            ((uint16_t*)base)[2 * off + 1] = half_bits(rnd_half(v.im)); break;
+    case 6: ((uint16_t*)base)[off] = bf16_bits(rnd_bf16(v.re)); break;
+    case 7: ((uint16_t*)base)[2 * off] = bf16_bits(rnd_bf16(v.re));
+            ((uint16_t*)base)[2 * off + 1] = bf16_bits(rnd_bf16(v.im)); break;
     }
 }
 
-/* Round a binary64 value to the computation precision (0 = single, 1 = double). */
-static double rnd_prec(double x, int prec) { return prec == 0 ? (double)(float)x : x; }
+/* Round a binary64 value to a precision (0 = single, 1 = double, 3 = binary16,
+ * 4 = bfloat16). */
+static double rnd_prec(double x, int prec) {
+    switch (prec) {
+    case 0: return (double)(float)x;
+    case 3: return rnd_half(x);
+    case 4: return rnd_bf16(x);
+    default: return x;
+    }
+}
+
+double oracle_round(double x, int prec) { return rnd_prec(x, prec); }
 
 /* Element (i, p) of op(X), where X is stored with strides (rs, cs) and trans in
  * {0:N, 1:T, 2:conj, 3:conj-trans}. For T and conj-trans, X is stored transposed. */
@@ -127,16 +219,16 @@ int oracle_mxgemm(int transa, int transb, int64_t m, int64_t n, int64_t k,
                   void* C, int dtC, int64_t rsC, int64_t csC,
                   int comp, double* c_exact, int nthreads, int literal_alpha) {
     if (transa < 0 || transa > 3 || transb < 0 || transb > 3) return 1;
-    if (dtA < 0 || dtA > 3 || dtB < 0 || dtB > 3 || dtC < 0 || dtC > 3) return 1;
-    if (comp < 0 || comp > 2 || m < 0 || n < 0 || k < 0) return 1;
+    if (dtA < 0 || dtA > 7 || dtB < 0 || dtB > 7 || dtC < 0 || dtC > 7) return 1;
+    if (comp < 0 || comp > 4 || m < 0 || n < 0 || k < 0) return 1;
     {
         int cse = oracle_case_of(dtC, dtA, dtB);
         if (!literal_alpha && alpha_im != 0.0 && cse != 0 && cse != 7) return 2;  /* Sec. 7.2 */
     }
-    if (comp == 2) comp = dt_is_double(dtC) ? 1 : 0;           /* Sec. 5.1.1 */
+    if (comp == 2) comp = dt_prec(dtC);                        /* Sec. 5.1.1 */
     {
         const int c_cplx = dt_is_complex(dtC);
-        const int precC = dt_is_double(dtC) ? 1 : 0;
+        const int precC = dt_prec(dtC);
         /* Sec. 7.1: alpha to the computation precision, beta to C's precision. */
         const double ar = rnd_prec(alpha_re, comp), ai = rnd_prec(alpha_im, comp);
         const double br = rnd_prec(beta_re, precC), bi = rnd_prec(beta_im, precC);

@@ -18,8 +18,14 @@ _SRC = os.path.join(_HERE, "mxg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libmxg_oracle.so")
 
-DT_CODES = {"s": 0, "d": 1, "c": 2, "z": 3}
-NP_OF_DT = {"s": np.float32, "d": np.float64, "c": np.complex64, "z": np.complex128}
+DT_CODES = {"s": 0, "d": 1, "c": 2, "z": 3, "h": 4, "k": 5, "b": 6, "w": 7}
+# numpy has no complex binary16 and no bfloat16: structured dtypes of 16-bit fields
+CHALF = np.dtype([("re", "<f2"), ("im", "<f2")])
+BF16 = np.dtype([("bits", "<u2")])
+CBF16 = np.dtype([("re", "<u2"), ("im", "<u2")])
+NP_OF_DT = {"s": np.float32, "d": np.float64, "c": np.complex64, "z": np.complex128,
+            "h": np.float16, "k": CHALF, "b": BF16, "w": CBF16}
+PREC_CODES = {"s": 0, "d": 1, "c": 2, "h": 3, "b": 4}
 TRANS_CODES = {"n": 0, "t": 1, "c": 2, "h": 3}
 
 _lock = threading.Lock()
@@ -59,15 +65,22 @@ def _load():
                                           dbl, dbl, vp, i32, i64, i64, i32, vp, i32, i32]
             lib.oracle_case_of.restype = i32
             lib.oracle_case_of.argtypes = [i32, i32, i32]
+            lib.oracle_round.restype = dbl
+            lib.oracle_round.argtypes = [dbl, i32]
             _lib = lib
     return _lib
 
 
 def _dt_of(arr):
     for k, v in NP_OF_DT.items():
-        if arr.dtype == v:
+        if arr.dtype == np.dtype(v):
             return k
     raise TypeError(f"unsupported dtype {arr.dtype}")
+
+
+def oracle_round(x, prec):
+    """The oracle's rounding of a binary64 value to precision 's', 'd', 'h' or 'b'."""
+    return _load().oracle_round(float(x), PREC_CODES[prec])
 
 
 def _strides(arr):
@@ -86,8 +99,8 @@ def oracle_mxgemm(transa, transb, alpha, A, B, beta, C, comp="c", nthreads=None,
     """C := beta*C + alpha*op(A)*op(B), in place on the numpy array C.
 
     ``transa``/``transb`` in {'n','t','c','h'} ('c' = conjugate without transpose,
-    'h' = conjugate transpose); ``comp`` in {'s','d','c'} where 'c' means "the
-    precision of C" (Sec. 5.1.1). ``alpha`` and ``beta`` are Python numbers (complex
+    'h' = conjugate transpose); ``comp`` in {'s','d','h','b','c'} where 'c' means "the
+    precision of C" (Sec. 5.1.1) and 'h' / 'b' are binary16 / bfloat16. ``alpha`` and ``beta`` are Python numbers (complex
     allowed). Returns the unrounded result C_new as a complex128 m x n array.
     """
     A = np.asarray(A); B = np.asarray(B)
@@ -101,7 +114,7 @@ def oracle_mxgemm(transa, transb, alpha, A, B, beta, C, comp="c", nthreads=None,
     if (B.shape[0] if tb in (1, 3) else B.shape[1]) != n or \
        (B.shape[1] if tb in (1, 3) else B.shape[0]) != k:
         raise ValueError("B shape does not match")
-    compc = {"s": 0, "d": 1, "c": 2}[comp]
+    compc = PREC_CODES[comp]
     if nthreads is None:
         nthreads = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
     out = np.zeros((m, n), dtype=np.complex128, order="F")

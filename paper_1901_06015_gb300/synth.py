@@ -14,17 +14,83 @@ alpha = beta = 1, Sec. 8.2.1; no dataset is involved):
 """
 import numpy as np
 
-NP_OF_DT = {"s": np.float32, "d": np.float64, "c": np.complex64, "z": np.complex128}
+# Storage datatypes: s, d, c, z (binary32/64, real/complex) and, beyond the paper's
+# four, h / k (binary16 real / complex) and b / w (bfloat16 real / complex). numpy has
+# no complex binary16 and no bfloat16, so those are structured dtypes of 16-bit fields
+# (bfloat16 fields hold bit patterns).
+CHALF = np.dtype([("re", "<f2"), ("im", "<f2")])
+BF16 = np.dtype([("bits", "<u2")])
+CBF16 = np.dtype([("re", "<u2"), ("im", "<u2")])
+NP_OF_DT = {"s": np.float32, "d": np.float64, "c": np.complex64, "z": np.complex128,
+            "h": np.float16, "k": CHALF, "b": BF16, "w": CBF16}
 DTS = ("s", "d", "c", "z")
+DTS_ALL = ("s", "d", "c", "z", "h", "k", "b", "w")
+COMPLEX_DTS = ("c", "z", "k", "w")
 
 
 def all_combos():
-    """All 128 labels ``cabx``: C, A, B storage datatypes then computation precision."""
+    """All 128 labels ``cabx`` of the paper: C, A, B storage datatypes (s, d, c, z) then
+    the computation precision (s, d)."""
     return [c + a + b + x for c in DTS for a in DTS for b in DTS for x in ("s", "d")]
 
 
+def all_combos_16():
+    """Labels with at least one 16-bit storage datatype or a 16-bit computation
+    precision (h: binary16, b: bfloat16)."""
+    out = []
+    for c in DTS_ALL:
+        for a in DTS_ALL:
+            for b in DTS_ALL:
+                for x in ("s", "d", "h", "b"):
+                    if x in ("h", "b") or any(t not in DTS for t in (c, a, b)):
+                        out.append(c + a + b + x)
+    return out
+
+
 def is_complex(dt):
-    return dt in ("c", "z")
+    return dt in COMPLEX_DTS
+
+
+def _bf16_bits_from_f32(x32):
+    """bfloat16 bit patterns (round-to-nearest-even) of binary32 values (input
+    generation only)."""
+    u = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def from_values(val, dt, order="F"):
+    """Store complex128 (or real) values in datatype dt, rounding to its precision."""
+    val = np.asarray(val)
+    if dt in ("s", "d", "c", "z", "h"):
+        v = val if is_complex(dt) else np.real(val)
+        return np.asarray(v, dtype=NP_OF_DT[dt], order=order)
+    out = np.empty(val.shape, dtype=NP_OF_DT[dt], order=order)
+    if dt == "k":
+        out["re"] = np.real(val).astype(np.float16)
+        out["im"] = np.imag(val).astype(np.float16)
+    elif dt == "b":
+        out["bits"] = _bf16_bits_from_f32(np.real(val).astype(np.float32))
+    else:
+        out["re"] = _bf16_bits_from_f32(np.real(val).astype(np.float32))
+        out["im"] = _bf16_bits_from_f32(np.imag(val).astype(np.float32))
+    return out
+
+
+def _bf16_to_f64(bits):
+    return (np.asarray(bits, dtype=np.uint32) << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def to_c128(arr, dt=None):
+    """Values of a stored matrix as complex128 (exact)."""
+    arr = np.asarray(arr)
+    if arr.dtype == CHALF:
+        return arr["re"].astype(np.float64) + 1j * arr["im"].astype(np.float64)
+    if arr.dtype == BF16:
+        return _bf16_to_f64(arr["bits"]).astype(np.complex128)
+    if arr.dtype == CBF16:
+        return _bf16_to_f64(arr["re"]) + 1j * _bf16_to_f64(arr["im"])
+    return arr.astype(np.complex128)
 
 
 def _component(rng, shape, dist):
@@ -40,14 +106,14 @@ def _component(rng, shape, dist):
 
 
 def matrix(rng, rows, cols, dt, dist="uniform", order="F"):
-    """One rows x cols matrix of storage datatype ``dt`` ('s','d','c','z')."""
+    """One rows x cols matrix of storage datatype ``dt``."""
     re = _component(rng, (rows, cols), dist)
     if is_complex(dt):
         im = _component(rng, (rows, cols), dist)
         val = re + 1j * im
     else:
         val = re
-    return np.asarray(val, dtype=NP_OF_DT[dt], order=order)
+    return from_values(val, dt, order)
 
 
 def problem(seed, combo, m, n, k, dist="uniform", transa="n", transb="n",

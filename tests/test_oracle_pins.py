@@ -17,7 +17,7 @@ from oracle import oracle_mxgemm, OracleError
 from paper_1901_06015_gb300 import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-CPLX = ("c", "z")
+CPLX = synth.COMPLEX_DTS
 
 
 # ---------------------------------------------------------------- exact brute force
@@ -432,3 +432,127 @@ def test_literal_alpha_agrees_with_paper_rule_for_real_alpha():
         r1 = oracle_mxgemm("n", "n", -1.5, A, B, 0.5, C1, comp=combo[3])
         r2 = oracle_mxgemm("n", "n", -1.5, A, B, 0.5, C2, comp=combo[3], literal_alpha=True)
         assert np.array_equal(r1, r2)
+
+
+# ---------------------------------------------------------------- 16-bit formats (Sec. 5.3)
+from oracle import oracle_round
+
+
+def _bf16_ref(x):
+    """bfloat16 round-to-nearest-even of a binary32-representable value, on its bits."""
+    u = int(np.array([x], dtype=np.float32).view(np.uint32)[0])
+    if (u & 0x7F800000) == 0x7F800000:
+        return float(np.float32(x))
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return float(np.array([u], dtype=np.uint32).view(np.float32)[0])
+
+
+def test_binary16_rounding_matches_numpy():
+    rng = np.random.default_rng(1)
+    xs = list(rng.standard_normal(4000) * 10.0 ** rng.uniform(-9, 6, 4000))
+    # exact ties between neighbouring binary16 values, subnormals, the overflow edge
+    h = np.arange(0, 0x7C00, 7, dtype=np.uint16).view(np.float16).astype(np.float64)
+    xs += list((h[:-1] + h[1:]) / 2) + [65504.0, 65519.99, 65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26]
+    for x in xs:
+        for v in (x, -x):
+            assert oracle_round(v, "h") == float(np.float16(v)), v
+
+
+def test_bfloat16_rounding_matches_bit_rule():
+    rng = np.random.default_rng(2)
+    xs = [float(np.float32(v)) for v in rng.standard_normal(4000) * 10.0 ** rng.uniform(-30, 30, 4000)]
+    b = (np.arange(0, 0x7F80, 5, dtype=np.uint32) << 16).view(np.float32).astype(np.float64)
+    xs += list((b[:-1] + b[1:]) / 2)                       # ties (representable in binary32)
+    tie = (2.0 - 2.0 ** -8) * 2.0 ** 127      # halfway between the largest finite value and 2^128
+    xs += [float(np.float32(1e-40)), (2.0 - 2.0 ** -7) * 2.0 ** 127]
+    for x in xs:
+        for v in (x, -x):
+            assert oracle_round(v, "b") == _bf16_ref(v), v
+    # the overflow edge (ties to even: the largest finite value has an odd significand)
+    assert oracle_round(tie, "b") == float("inf")
+    assert oracle_round(np.nextafter(tie, 0.0), "b") == (2.0 - 2.0 ** -7) * 2.0 ** 127
+    assert oracle_round(-tie, "b") == float("-inf")
+
+
+_SAMPLE16 = [c for i, c in enumerate(synth.all_combos_16()) if i % 11 == 0]
+
+
+def _rnd16(x, prec):
+    if prec == "s":
+        return float(np.float32(x))
+    if prec == "h":
+        return float(np.float16(x))
+    if prec == "b":
+        return _bf16_ref(x)
+    return float(x)
+
+
+@pytest.mark.parametrize("combo", _SAMPLE16)
+def test_bruteforce_exact_16bit_combos(combo):
+    """Tiny dyadic inputs in 16-bit storage and precisions: the oracle equals the exact
+    rational statement of the case table bit for bit, and rounds C correctly."""
+    rng = np.random.default_rng(abs(hash(combo + "16")) % (2 ** 32))
+    dc, da, db, x = combo
+    prec = {"s": "s", "c": "s", "d": "d", "z": "d", "h": "h", "k": "h", "b": "b", "w": "b"}
+    for ta, tb in (("n", "n"), ("t", "h"), ("c", "t")):
+        m, n, k = (int(v) for v in rng.integers(1, 4, size=3))
+        def dy(shape, dt):
+            re = rng.integers(-8, 9, size=shape) / 4.0
+            im = rng.integers(-8, 9, size=shape) / 4.0 if synth.is_complex(dt) else 0.0
+            return synth.from_values(re + 1j * im, dt)
+        A = dy((k, m) if ta in "th" else (m, k), da)
+        B = dy((n, k) if tb in "th" else (k, n), db)
+        C0 = dy((m, n), dc)
+        case = oracle.oracle_case_of(dc, da, db)
+        alpha = (0.75 + 0.5j) if case in (0, 7) else -1.5
+        beta = [0.0, -0.5, 1.0, 0.25 - 0.75j][int(rng.integers(0, 4))]
+        Cw = C0.copy()
+        out = oracle_mxgemm(ta, tb, alpha, A, B, beta, Cw, comp=x)
+        # the rational statement, with the 16-bit cast done by numpy / the bit rule
+        opA, opB = synth.to_c128(A), synth.to_c128(B)
+        if ta in "th": opA = opA.T
+        if tb in "th": opB = opB.T
+        if ta in "ch": opA = np.conj(opA)
+        if tb in "ch": opB = np.conj(opB)
+        comp = prec[dc] if x == "c" else x
+        exp = frac_reference(combo if x in "sd" else dc + da + db + "d", "n", "n",
+                             complex(_rnd16(np.real(alpha), comp), _rnd16(np.imag(alpha), comp)),
+                             opA, opB, complex(_rnd16(np.real(beta), prec[dc]), _rnd16(np.imag(beta), prec[dc])),
+                             synth.to_c128(C0) if synth.is_complex(dc) else synth.to_c128(C0).real)
+        got = synth.to_c128(Cw)
+        for i in range(m):
+            for j in range(n):
+                er, ei = float(exp[i][j][0]), float(exp[i][j][1])
+                assert out[i, j].real == er and out[i, j].imag == ei, (combo, ta, tb, i, j)
+                assert got[i, j].real == _rnd16(er, prec[dc]), (combo, i, j)
+                if synth.is_complex(dc):
+                    assert got[i, j].imag == _rnd16(ei, prec[dc])
+
+
+@pytest.mark.parametrize("combo", _SAMPLE16)
+def test_identity_16bit_combos(combo):
+    """The 16-bit combinations equal a complex128 numpy gemm on operands cast to the
+    computation precision (numpy's float16 / the bfloat16 bit rule) and projected."""
+    dc, da, db, x = combo
+    prec = {"s": "s", "c": "s", "d": "d", "z": "d", "h": "h", "k": "h", "b": "b", "w": "b"}
+    comp = prec[dc] if x == "c" else x
+    A, B, C0 = synth.problem(21, combo, 13, 11, 17)
+    cast = np.vectorize(lambda v: _rnd16(v, comp))
+    Ah = cast(synth.to_c128(A).real) + 1j * cast(synth.to_c128(A).imag)
+    Bh = cast(synth.to_c128(B).real) + 1j * cast(synth.to_c128(B).imag)
+    case = oracle.oracle_case_of(dc, da, db)
+    alpha = (1.25 - 0.5j) if case == 7 else 1.5
+    ah = complex(_rnd16(np.real(alpha), comp), _rnd16(np.imag(alpha), comp))
+    bh = complex(_rnd16(-0.5, prec[dc]), _rnd16(0.25, prec[dc]))
+    C = synth.to_c128(C0)
+    if not synth.is_complex(dc):
+        if not synth.is_complex(db):
+            Ah = Ah.real
+        if not synth.is_complex(da):
+            Bh = Bh.real
+        want = bh.real * C.real + ah.real * (Ah @ Bh).real
+    else:
+        want = bh * C + ah * (Ah @ Bh)
+    got = oracle_mxgemm("n", "n", alpha, A, B, -0.5 + 0.25j, C0.copy(), comp=x)
+    scale = abs(alpha) * np.linalg.norm(Ah) * np.linalg.norm(Bh) + np.linalg.norm(C)
+    assert np.linalg.norm(got - want) / scale < 1e-14
