@@ -55,26 +55,34 @@
 extern "C" {
 #endif
 
-/* Storage datatypes (Sec. 3: domain x precision). */
-enum { MXG_S = 0, MXG_D = 1, MXG_C = 2, MXG_Z = 3 };
+/* Storage datatypes (Sec. 3: domain x precision). Beyond the paper's four, the
+ * 16-bit precisions of Sec. 5.3: MXG_H real binary16, MXG_K complex binary16, MXG_B
+ * real bfloat16, MXG_W complex bfloat16 (a complex element is (re, im), 4 bytes). */
+enum { MXG_S = 0, MXG_D = 1, MXG_C = 2, MXG_Z = 3, MXG_H = 4, MXG_K = 5, MXG_B = 6, MXG_W = 7 };
 
 /* Transposition values (Sec. 3, incl. conjugation without transposition). */
 enum { MXG_NOTRANS = 0, MXG_TRANS = 1, MXG_CONJ = 2, MXG_CONJTRANS = 3 };
 
-/* Computation precision (Sec. 5.1.1). MXG_PREC_OF_C: that of C's storage. */
-enum { MXG_PREC_S = 0, MXG_PREC_D = 1, MXG_PREC_OF_C = 2 };
+/* Computation precision (Sec. 5.1.1). MXG_PREC_OF_C: that of C's storage.
+ * MXG_PREC_H / MXG_PREC_B (Sec. 5.3): A and B are rounded to binary16 / bfloat16 and
+ * the products are summed in FP32 on the tensor cores (method MXG_METHOD_TC16); alpha
+ * is rounded to that precision. */
+enum { MXG_PREC_S = 0, MXG_PREC_D = 1, MXG_PREC_OF_C = 2, MXG_PREC_H = 3, MXG_PREC_B = 4 };
 
 /* Contraction methods. FFMA: plain FP32 fused multiply-add (single);
  * TF32X3 / BF16X3: split-precision tensor-core products hi*hi + hi*lo + lo*hi with
  * FP32 accumulation (single); DMMA: FP64 tensor-core mma (double); DFMA: plain FP64
- * fused multiply-add (double). AUTO picks the fastest method of the precision. */
+ * fused multiply-add (double); TC16: one tensor-core pass on binary16 / bfloat16
+ * operands with FP32 accumulation (computation precision h / b). AUTO picks FFMA for
+ * single, DFMA for double and TC16 for the 16-bit precisions. */
 enum {
   MXG_METHOD_AUTO = 0,
   MXG_METHOD_FFMA = 1,
   MXG_METHOD_TF32X3 = 2,
   MXG_METHOD_BF16X3 = 3,
   MXG_METHOD_DMMA = 4,
-  MXG_METHOD_DFMA = 5
+  MXG_METHOD_DFMA = 5,
+  MXG_METHOD_TC16 = 6
 };
 
 /* Status codes. */
@@ -104,7 +112,7 @@ typedef struct mxg_context* mxg_handle;
 /* Description of the real gemm a call reduces to (host-side planning only). */
 typedef struct {
   int domain_case;          /* MXG_CASE_* (Fig. "mixeddom") */
-  int comp_prec;            /* resolved computation precision: MXG_PREC_S or MXG_PREC_D */
+  int comp_prec;            /* resolved computation precision: MXG_PREC_S, _D, _H or _B */
   int method;               /* resolved MXG_METHOD_* */
   int whole_op_transposed;  /* 1 if computed as C^T := op(B)^T op(A)^T (Sec. 2.2.5) */
   int64_t Mr, Nr, Kr;       /* dimensions of the real product (M', N', K') */

@@ -9,6 +9,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "mxg_internal.h"
 #include "context.h"
 #include "plan.h"
@@ -24,10 +27,18 @@ static int cuda_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? MXG_ENOMEM : MXG_ECUDA;
 }
 
-static bool dt_ok(int dt) { return dt >= MXG_S && dt <= MXG_Z; }
+static bool dt_ok(int dt) { return dt >= MXG_S && dt <= MXG_W; }
 static bool trans_ok(int t) { return t >= MXG_NOTRANS && t <= MXG_CONJTRANS; }
-static bool is_cplx(int dt) { return dt == MXG_C || dt == MXG_Z; }
-static bool is_dbl(int dt) { return dt == MXG_D || dt == MXG_Z; }
+static bool is_cplx(int dt) { return dt == MXG_C || dt == MXG_Z || dt == MXG_K || dt == MXG_W; }
+// storage precision of a datatype as an MXG_PREC_* code
+static int prec_of_dt(int dt) {
+  switch (dt) {
+    case MXG_D: case MXG_Z: return MXG_PREC_D;
+    case MXG_H: case MXG_K: return MXG_PREC_H;
+    case MXG_B: case MXG_W: return MXG_PREC_B;
+    default: return MXG_PREC_S;
+  }
+}
 static bool is_t(int t) { return t == MXG_TRANS || t == MXG_CONJTRANS; }
 static bool is_conj(int t) { return t == MXG_CONJ || t == MXG_CONJTRANS; }
 static int flip_t(int t) {  // op(X)^T expressed as a trans value on the same storage
@@ -38,7 +49,15 @@ static int flip_t(int t) {  // op(X)^T expressed as a trans value on the same st
     default: return MXG_CONJ;
   }
 }
-static double rnd(double x, bool dbl) { return dbl ? x : static_cast<double>(static_cast<float>(x)); }
+// Round (RN-even) to an MXG_PREC_* precision, with CUDA's host conversions for 16 bits.
+static double rnd_p(double x, int prec) {
+  switch (prec) {
+    case MXG_PREC_D: return x;
+    case MXG_PREC_H: return static_cast<double>(__half2float(__double2half(x)));
+    case MXG_PREC_B: return static_cast<double>(__bfloat162float(__double2bfloat16(x)));
+    default: return static_cast<double>(static_cast<float>(x));
+  }
+}
 static int64_t round_up(int64_t x, int64_t t) { return (x + t - 1) / t * t; }
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
@@ -69,8 +88,8 @@ static size_t esz_of(const Plan& P) { return P.comp_double ? 8 : 4; }
 int make_plan(const Call& c, int method, Plan* p) {
   if (!trans_ok(c.transa) || !trans_ok(c.transb)) return MXG_EINVAL;
   if (!dt_ok(c.dtA) || !dt_ok(c.dtB) || !dt_ok(c.dtC)) return MXG_EINVAL;
-  if (c.comp < MXG_PREC_S || c.comp > MXG_PREC_OF_C) return MXG_EINVAL;
-  if (method < MXG_METHOD_AUTO || method > MXG_METHOD_DFMA) return MXG_EINVAL;
+  if (c.comp < MXG_PREC_S || c.comp > MXG_PREC_B) return MXG_EINVAL;
+  if (method < MXG_METHOD_AUTO || method > MXG_METHOD_TC16) return MXG_EINVAL;
   if (c.m < 0 || c.n < 0 || c.k < 0) return MXG_EINVAL;
   const int64_t a_rows = is_t(c.transa) ? c.k : c.m, a_cols = is_t(c.transa) ? c.m : c.k;
   const int64_t b_rows = is_t(c.transb) ? c.n : c.k, b_cols = is_t(c.transb) ? c.k : c.n;
@@ -88,20 +107,25 @@ int make_plan(const Call& c, int method, Plan* p) {
   if (!c.literal_alpha && c.alpha_im != 0.0 && P.domain_case != MXG_CASE_0 && P.domain_case != MXG_CASE_3)
     return MXG_ECOMPLEX_ALPHA;
   // Sec. 5.1.1: the computation precision defaults to C's storage precision.
-  P.comp_double = (c.comp == MXG_PREC_OF_C) ? is_dbl(c.dtC) : (c.comp == MXG_PREC_D);
+  P.comp = (c.comp == MXG_PREC_OF_C) ? prec_of_dt(c.dtC) : c.comp;
+  P.comp_double = (P.comp == MXG_PREC_D);
+  const bool comp16 = (P.comp == MXG_PREC_H || P.comp == MXG_PREC_B);
   // AUTO: the faster plain form of each precision on GB300 (measured: DFMA 1.25 vs
-  // DMMA 1.10 TF/s, both on the FP64 pipe).
-  if (method == MXG_METHOD_AUTO) method = P.comp_double ? MXG_METHOD_DFMA : MXG_METHOD_FFMA;
+  // DMMA 1.10 TF/s, both on the FP64 pipe); the 16-bit precisions run on the tensor
+  // cores.
+  if (method == MXG_METHOD_AUTO)
+    method = comp16 ? MXG_METHOD_TC16 : (P.comp_double ? MXG_METHOD_DFMA : MXG_METHOD_FFMA);
   const bool m_double = (method == MXG_METHOD_DMMA || method == MXG_METHOD_DFMA);
-  if (m_double != P.comp_double) return MXG_EINVAL;
+  const bool m_16 = (method == MXG_METHOD_TC16);
+  if (m_double != P.comp_double || m_16 != comp16) return MXG_EINVAL;
   P.method = method;
 
   // Sec. 7.1: alpha in the computation precision, beta in C's storage precision.
-  P.ar = rnd(c.alpha_re, P.comp_double);
+  P.ar = rnd_p(c.alpha_re, P.comp);
   P.ai = (P.domain_case == MXG_CASE_3 || (c.literal_alpha && P.domain_case != MXG_CASE_0))
-             ? rnd(c.alpha_im, P.comp_double) : 0.0;                            // case 0 projects
-  P.br = rnd(c.beta_re, is_dbl(c.dtC));
-  P.bi = is_cplx(c.dtC) ? rnd(c.beta_im, is_dbl(c.dtC)) : 0.0;                   // real C projects
+             ? rnd_p(c.alpha_im, P.comp) : 0.0;                                 // case 0 projects
+  P.br = rnd_p(c.beta_re, prec_of_dt(c.dtC));
+  P.bi = is_cplx(c.dtC) ? rnd_p(c.beta_im, prec_of_dt(c.dtC)) : 0.0;            // real C projects
   P.beta_zero = (P.br == 0.0 && P.bi == 0.0);
   P.alpha_zero = (P.ar == 0.0 && P.ai == 0.0);
   P.real_products = 1;
@@ -153,14 +177,17 @@ int make_plan(const Call& c, int method, Plan* p) {
   P.Mp = round_up(P.Mr, t.tm);
   P.Np = round_up(P.Nr, t.tn);
   P.Kp = round_up(P.Kr, t.tk);
-  if (method == MXG_METHOD_TF32X3 || method == MXG_METHOD_BF16X3) {
-    // two planes (hi, lo) per operand, K-major, for TMA
-    P.split = (method == MXG_METHOD_BF16X3) ? SPLIT_BF16 : SPLIT_TF32;
-    const size_t esz = (P.split == SPLIT_BF16) ? 2 : 4;
+  if (method == MXG_METHOD_TF32X3 || method == MXG_METHOD_BF16X3 || method == MXG_METHOD_TC16) {
+    // K-major planes for TMA: hi and lo for the split forms, one plane for TC16
+    P.split = (method == MXG_METHOD_BF16X3) ? SPLIT_BF16
+              : (method == MXG_METHOD_TF32X3) ? SPLIT_TF32
+              : (P.comp == MXG_PREC_H) ? SPLIT_F16_ONE : SPLIT_BF16_ONE;
+    const size_t esz = (P.split == SPLIT_TF32) ? 4 : 2;
+    const int planes = (method == MXG_METHOD_TC16) ? 1 : 2;
     P.plane_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
     P.plane_b = align256(static_cast<size_t>(P.Kp) * P.Np * esz);
-    P.bytes_a = 2 * P.plane_a;
-    P.bytes_b = 2 * P.plane_b;
+    P.bytes_a = planes * P.plane_a;
+    P.bytes_b = planes * P.plane_b;
   } else {
     const size_t esz = P.comp_double ? 8 : 4;
     P.bytes_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
@@ -224,7 +251,8 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   pa.layout = LAYOUT_MN_MAJOR; pa.split = SPLIT_NONE;
   pa.fold = P.fold_a; pa.fold_re = P.ar; pa.fold_im = P.ai;
   if (P.split != SPLIT_NONE) {
-    pa.dst_lo = base + P.plane_a; pa.ld = P.Kp; pa.layout = LAYOUT_K_MAJOR; pa.split = P.split;
+    pa.dst_lo = (P.method == MXG_METHOD_TC16) ? nullptr : base + P.plane_a;
+    pa.ld = P.Kp; pa.layout = LAYOUT_K_MAJOR; pa.split = P.split;
   }
   int st = cuda_status(launch_pack(pa, P.comp_double, s));
   if (st) return st;
@@ -236,15 +264,18 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   pb.layout = LAYOUT_MN_MAJOR; pb.split = SPLIT_NONE;
   pb.fold = P.fold_b; pb.fold_re = P.ar; pb.fold_im = P.ai;
   if (P.split != SPLIT_NONE) {
-    pb.dst_lo = base + P.bytes_a + P.plane_b; pb.ld = P.Kp; pb.layout = LAYOUT_K_MAJOR; pb.split = P.split;
+    pb.dst_lo = (P.method == MXG_METHOD_TC16) ? nullptr : base + P.bytes_a + P.plane_b;
+    pb.ld = P.Kp; pb.layout = LAYOUT_K_MAJOR; pb.split = P.split;
   }
   st = cuda_status(launch_pack(pb, P.comp_double, s));
   if (st) return st;
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (P.split != SPLIT_NONE) {
-    const void* planes[4] = {base, base + P.plane_a, base + P.bytes_a, base + P.bytes_a + P.plane_b};
-    const cudaError_t e = launch_gemm_tc(P.method, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P),
-                                         dev_err, s);
+    const bool one = (P.method == MXG_METHOD_TC16);
+    const void* planes[4] = {base, one ? base : base + P.plane_a, base + P.bytes_a,
+                             one ? base + P.bytes_a : base + P.bytes_a + P.plane_b};
+    const cudaError_t e = launch_gemm_tc(P.method, P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp,
+                                         plan_epilogue(P), dev_err, s);
     return e == cudaErrorNotSupported ? MXG_ENOTSUP : cuda_status(e);
   }
   GemmArgs g;
@@ -340,7 +371,7 @@ int mxg_plan(int method, int transa, int transb, int64_t m, int64_t n, int64_t k
   if (st != MXG_OK) return st;
   if (info) {
     info->domain_case = P.domain_case;
-    info->comp_prec = P.comp_double ? MXG_PREC_D : MXG_PREC_S;
+    info->comp_prec = P.comp;
     info->method = P.method;
     info->whole_op_transposed = P.swapped ? 1 : 0;
     info->Mr = P.Mr; info->Nr = P.Nr; info->Kr = P.Kr;

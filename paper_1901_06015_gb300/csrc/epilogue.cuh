@@ -4,6 +4,11 @@
 // alpha*AB cast to C's precision before it is accumulated).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "mxg_internal.h"
 #include "../../include/mxgemm.h"
 
@@ -13,6 +18,30 @@ template <int CDT> struct CStore { using T = float; static constexpr bool cplx =
 template <> struct CStore<MXG_D> { using T = double; static constexpr bool cplx = false; };
 template <> struct CStore<MXG_C> { using T = float; static constexpr bool cplx = true; };
 template <> struct CStore<MXG_Z> { using T = double; static constexpr bool cplx = true; };
+template <> struct CStore<MXG_H> { using T = __half; static constexpr bool cplx = false; };
+template <> struct CStore<MXG_K> { using T = __half; static constexpr bool cplx = true; };
+template <> struct CStore<MXG_B> { using T = __nv_bfloat16; static constexpr bool cplx = false; };
+template <> struct CStore<MXG_W> { using T = __nv_bfloat16; static constexpr bool cplx = true; };
+
+template <int V> using IC = std::integral_constant<int, V>;
+
+// Call f(IC<C datatype>, IC<output mode>) for the 16 valid pairs: a real C takes
+// OUT_REAL, a complex C one of OUT_RE_ONLY / OUT_ROWPAIR / OUT_COLPAIR. Returns false
+// for any other pair.
+template <class F>
+__host__ __device__ __forceinline__ bool with_c_mode(int cdt, int mode, F&& f) {
+  switch (cdt * 4 + mode) {
+#define MXG_CM(C, M) \
+    case C * 4 + M: f(IC<C>{}, IC<M>{}); return true;
+    MXG_CM(MXG_S, OUT_REAL) MXG_CM(MXG_D, OUT_REAL) MXG_CM(MXG_H, OUT_REAL) MXG_CM(MXG_B, OUT_REAL)
+    MXG_CM(MXG_C, OUT_RE_ONLY) MXG_CM(MXG_C, OUT_ROWPAIR) MXG_CM(MXG_C, OUT_COLPAIR)
+    MXG_CM(MXG_Z, OUT_RE_ONLY) MXG_CM(MXG_Z, OUT_ROWPAIR) MXG_CM(MXG_Z, OUT_COLPAIR)
+    MXG_CM(MXG_K, OUT_RE_ONLY) MXG_CM(MXG_K, OUT_ROWPAIR) MXG_CM(MXG_K, OUT_COLPAIR)
+    MXG_CM(MXG_W, OUT_RE_ONLY) MXG_CM(MXG_W, OUT_ROWPAIR) MXG_CM(MXG_W, OUT_COLPAIR)
+#undef MXG_CM
+    default: return false;
+  }
+}
 
 // Explicitly rounded products and sums (round-to-nearest-even). The compiler never
 // fuses these into FMAs, so every rounding the paper's order prescribes happens, and
@@ -23,6 +52,25 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ __half mul_rn(__half a, __half b) { return __hmul_rn(a, b); }
+__device__ __forceinline__ __half add_rn(__half a, __half b) { return __hadd_rn(a, b); }
+__device__ __forceinline__ __half sub_rn(__half a, __half b) { return __hsub_rn(a, b); }
+__device__ __forceinline__ __nv_bfloat16 mul_rn(__nv_bfloat16 a, __nv_bfloat16 b) { return __hmul_rn(a, b); }
+__device__ __forceinline__ __nv_bfloat16 add_rn(__nv_bfloat16 a, __nv_bfloat16 b) { return __hadd_rn(a, b); }
+__device__ __forceinline__ __nv_bfloat16 sub_rn(__nv_bfloat16 a, __nv_bfloat16 b) { return __hsub_rn(a, b); }
+
+// Conversion (RN-even) to C's storage type.
+template <typename CT> __device__ __forceinline__ CT to_ct(float x);
+template <typename CT> __device__ __forceinline__ CT to_ct(double x);
+template <> __device__ __forceinline__ float to_ct<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_ct<float>(double x) { return static_cast<float>(x); }
+template <> __device__ __forceinline__ double to_ct<double>(float x) { return x; }
+template <> __device__ __forceinline__ double to_ct<double>(double x) { return x; }
+template <> __device__ __forceinline__ __half to_ct<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __half to_ct<__half>(double x) { return __double2half(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_ct<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_ct<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
 
 // Update C(i, j) with the product value (pr, pi), both in the computation precision
 // AccT. pi is ignored unless MODE pairs two real results into one complex value.
@@ -36,8 +84,8 @@ __device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j
   CT* c = static_cast<CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
   if constexpr (!CStore<CDT>::cplx) {
     // C real: alpha and beta projected onto the real line (Sec. 7.2).
-    const CT t = static_cast<CT>(mul_rn(ar, pr));
-    c[0] = e.beta_zero ? t : add_rn(mul_rn(static_cast<CT>(e.br), c[0]), t);
+    const CT t = to_ct<CT>(mul_rn(ar, pr));
+    c[0] = e.beta_zero ? t : add_rn(mul_rn(to_ct<CT>(e.br), c[0]), t);
   } else {
     AccT tr, ti;
     const AccT ai_ = static_cast<AccT>(e.ai);
@@ -49,12 +97,12 @@ __device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j
       tr = sub_rn(mul_rn(ar, pr), mul_rn(ai, pi));  // complex alpha honoured (case 3)
       ti = add_rn(mul_rn(ar, pi), mul_rn(ai, pr));  // ai == 0 otherwise
     }
-    const CT tcr = static_cast<CT>(tr), tci = static_cast<CT>(ti);
+    const CT tcr = to_ct<CT>(tr), tci = to_ct<CT>(ti);
     if (e.beta_zero) {
       c[0] = tcr;
-      c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? CT(0) : tci;
+      c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? to_ct<CT>(0.0f) : tci;
     } else {
-      const CT br = static_cast<CT>(e.br), bi = static_cast<CT>(e.bi);
+      const CT br = to_ct<CT>(e.br), bi = to_ct<CT>(e.bi);
       const CT cr = c[0], ci = c[1];
       const CT bcr = sub_rn(mul_rn(br, cr), mul_rn(bi, ci));
       const CT bci = add_rn(mul_rn(br, ci), mul_rn(bi, cr));

@@ -117,17 +117,7 @@ __device__ __forceinline__ void dmma_epilogue(const EpiArgs& e, int64_t m0, int6
 
 __device__ __forceinline__ void dmma_epilogue_rt(int cdt, int mode, const EpiArgs& e, int64_t m0, int64_t n0,
                                                  const double* Cs) {
-  switch (cdt * 4 + mode) {
-    case MXG_S * 4 + OUT_REAL: dmma_epilogue<MXG_S, OUT_REAL>(e, m0, n0, Cs); break;
-    case MXG_D * 4 + OUT_REAL: dmma_epilogue<MXG_D, OUT_REAL>(e, m0, n0, Cs); break;
-    case MXG_C * 4 + OUT_RE_ONLY: dmma_epilogue<MXG_C, OUT_RE_ONLY>(e, m0, n0, Cs); break;
-    case MXG_C * 4 + OUT_ROWPAIR: dmma_epilogue<MXG_C, OUT_ROWPAIR>(e, m0, n0, Cs); break;
-    case MXG_C * 4 + OUT_COLPAIR: dmma_epilogue<MXG_C, OUT_COLPAIR>(e, m0, n0, Cs); break;
-    case MXG_Z * 4 + OUT_RE_ONLY: dmma_epilogue<MXG_Z, OUT_RE_ONLY>(e, m0, n0, Cs); break;
-    case MXG_Z * 4 + OUT_ROWPAIR: dmma_epilogue<MXG_Z, OUT_ROWPAIR>(e, m0, n0, Cs); break;
-    case MXG_Z * 4 + OUT_COLPAIR: dmma_epilogue<MXG_Z, OUT_COLPAIR>(e, m0, n0, Cs); break;
-    default: break;
-  }
+  with_c_mode(cdt, mode, [&](auto C, auto M) { dmma_epilogue<decltype(C)::value, decltype(M)::value>(e, m0, n0, Cs); });
 }
 
 template <int CDT, int MODE>
@@ -184,18 +174,10 @@ cudaError_t launch_dmma_partial(const GemmArgs& g, int64_t kslice, double* ws, d
 }
 
 cudaError_t launch_dmma(int mode, int cdt, const GemmArgs& g, cudaStream_t s, dim3 grid) {
-  switch (cdt * 4 + mode) {
-    case MXG_S * 4 + OUT_REAL: dmma_gemm<MXG_S, OUT_REAL><<<grid, 128, 0, s>>>(g); break;
-    case MXG_D * 4 + OUT_REAL: dmma_gemm<MXG_D, OUT_REAL><<<grid, 128, 0, s>>>(g); break;
-    case MXG_C * 4 + OUT_RE_ONLY: dmma_gemm<MXG_C, OUT_RE_ONLY><<<grid, 128, 0, s>>>(g); break;
-    case MXG_C * 4 + OUT_ROWPAIR: dmma_gemm<MXG_C, OUT_ROWPAIR><<<grid, 128, 0, s>>>(g); break;
-    case MXG_C * 4 + OUT_COLPAIR: dmma_gemm<MXG_C, OUT_COLPAIR><<<grid, 128, 0, s>>>(g); break;
-    case MXG_Z * 4 + OUT_RE_ONLY: dmma_gemm<MXG_Z, OUT_RE_ONLY><<<grid, 128, 0, s>>>(g); break;
-    case MXG_Z * 4 + OUT_ROWPAIR: dmma_gemm<MXG_Z, OUT_ROWPAIR><<<grid, 128, 0, s>>>(g); break;
-    case MXG_Z * 4 + OUT_COLPAIR: dmma_gemm<MXG_Z, OUT_COLPAIR><<<grid, 128, 0, s>>>(g); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  const bool ok = with_c_mode(cdt, mode, [&](auto C, auto M) {
+    dmma_gemm<decltype(C)::value, decltype(M)::value><<<grid, 128, 0, s>>>(g);
+  });
+  return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dmma_grouped(const GroupProb* probs, const GroupTile* tiles, int ntiles, int* counter, int sched,

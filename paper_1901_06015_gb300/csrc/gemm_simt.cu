@@ -146,21 +146,13 @@ __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int6
   }
 }
 
-// Runtime dispatch over the 8 valid (C datatype, output mode) pairs, once per tile.
+// Runtime dispatch over the valid (C datatype, output mode) pairs, once per tile.
 template <typename T, int H>
 __device__ __forceinline__ void simt_epilogue_rt(int cdt, int mode, const EpiArgs& e, int64_t m0, int64_t n0,
                                                  const T (&acc)[2 * H][2 * H]) {
-  switch (cdt * 4 + mode) {
-    case MXG_S * 4 + OUT_REAL: simt_epilogue<T, H, MXG_S, OUT_REAL>(e, m0, n0, acc); break;
-    case MXG_D * 4 + OUT_REAL: simt_epilogue<T, H, MXG_D, OUT_REAL>(e, m0, n0, acc); break;
-    case MXG_C * 4 + OUT_RE_ONLY: simt_epilogue<T, H, MXG_C, OUT_RE_ONLY>(e, m0, n0, acc); break;
-    case MXG_C * 4 + OUT_ROWPAIR: simt_epilogue<T, H, MXG_C, OUT_ROWPAIR>(e, m0, n0, acc); break;
-    case MXG_C * 4 + OUT_COLPAIR: simt_epilogue<T, H, MXG_C, OUT_COLPAIR>(e, m0, n0, acc); break;
-    case MXG_Z * 4 + OUT_RE_ONLY: simt_epilogue<T, H, MXG_Z, OUT_RE_ONLY>(e, m0, n0, acc); break;
-    case MXG_Z * 4 + OUT_ROWPAIR: simt_epilogue<T, H, MXG_Z, OUT_ROWPAIR>(e, m0, n0, acc); break;
-    case MXG_Z * 4 + OUT_COLPAIR: simt_epilogue<T, H, MXG_Z, OUT_COLPAIR>(e, m0, n0, acc); break;
-    default: break;
-  }
+  with_c_mode(cdt, mode, [&](auto C, auto M) {
+    simt_epilogue<T, H, decltype(C)::value, decltype(M)::value>(e, m0, n0, acc);
+  });
 }
 
 template <typename T, int H, int CDT, int MODE>
@@ -250,36 +242,6 @@ __global__ void scale_c_kernel(EpiArgs e) {
   }
 }
 
-template <typename T, int H, int CDT>
-cudaError_t launch_simt_mode(int mode, const GemmArgs& g, cudaStream_t s, dim3 grid) {
-  switch (mode) {
-    case OUT_REAL: simt_gemm<T, H, CDT, OUT_REAL><<<grid, 256, 0, s>>>(g); break;
-    case OUT_RE_ONLY: simt_gemm<T, H, CDT, OUT_RE_ONLY><<<grid, 256, 0, s>>>(g); break;
-    case OUT_ROWPAIR: simt_gemm<T, H, CDT, OUT_ROWPAIR><<<grid, 256, 0, s>>>(g); break;
-    case OUT_COLPAIR: simt_gemm<T, H, CDT, OUT_COLPAIR><<<grid, 256, 0, s>>>(g); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-template <int CDT>
-cudaError_t launch_for_c(int method, int mode, const GemmArgs& g, cudaStream_t s) {
-  const TileCfg t = tile_cfg(method);
-  const int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
-  if (gx <= 0 || gy <= 0) return cudaSuccess;
-  if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
-  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
-  // Real C only takes OUT_REAL; complex C never does.
-  if (!CStore<CDT>::cplx && mode != OUT_REAL) return cudaErrorInvalidValue;
-  if (CStore<CDT>::cplx && mode == OUT_REAL) return cudaErrorInvalidValue;
-  switch (method) {
-    case MXG_METHOD_FFMA: return launch_simt_mode<float, 4, CDT>(mode, g, s, grid);
-    case MXG_METHOD_DFMA: return launch_simt_mode<double, 2, CDT>(mode, g, s, grid);
-    case MXG_METHOD_DMMA: return launch_dmma(mode, CDT, g, s, grid);
-  }
-  return cudaErrorInvalidValue;
-}
-
 }  // namespace
 
 TileCfg tile_cfg(int method) {
@@ -289,6 +251,7 @@ TileCfg tile_cfg(int method) {
     case MXG_METHOD_DMMA: return {64, 64, 16};
     case MXG_METHOD_TF32X3: return {128, 256, 16};   // tcgen05 tile 128 x 256, 64-byte k rows
     case MXG_METHOD_BF16X3: return {128, 256, 32};
+    case MXG_METHOD_TC16: return {128, 256, 32};
   }
   return {128, 128, 8};
 }
@@ -304,33 +267,31 @@ int variant_tile(int variant) {
 }
 
 cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, cudaStream_t s) {
-  switch (c_dt) {
-    case MXG_S: return launch_for_c<MXG_S>(method, mode, g, s);
-    case MXG_D: return launch_for_c<MXG_D>(method, mode, g, s);
-    case MXG_C: return launch_for_c<MXG_C>(method, mode, g, s);
-    case MXG_Z: return launch_for_c<MXG_Z>(method, mode, g, s);
-  }
-  return cudaErrorInvalidValue;
+  const TileCfg t = tile_cfg(method);
+  const int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
+  if (gx <= 0 || gy <= 0) return cudaSuccess;
+  if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
+  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
+  if (method == MXG_METHOD_DMMA) return launch_dmma(mode, c_dt, g, s, grid);
+  if (method != MXG_METHOD_FFMA && method != MXG_METHOD_DFMA) return cudaErrorInvalidValue;
+  const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto M) {
+    constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
+    if (method == MXG_METHOD_FFMA) simt_gemm<float, 4, CDT, MODE><<<grid, 256, 0, s>>>(g);
+    else simt_gemm<double, 2, CDT, MODE><<<grid, 256, 0, s>>>(g);
+  });
+  return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
 template <typename T>
 static cudaError_t launch_reduce(int c_dt, int mode, const T* ws, int splits, int64_t Mp, int64_t Np, const EpiArgs& e,
-                          cudaStream_t s) {
+                                 cudaStream_t s) {
   const int64_t total = e.m * e.n;
   if (total <= 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
-  switch (c_dt * 4 + mode) {
-    case MXG_S * 4 + OUT_REAL: splitk_reduce<T, MXG_S, OUT_REAL><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_D * 4 + OUT_REAL: splitk_reduce<T, MXG_D, OUT_REAL><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_C * 4 + OUT_RE_ONLY: splitk_reduce<T, MXG_C, OUT_RE_ONLY><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_C * 4 + OUT_ROWPAIR: splitk_reduce<T, MXG_C, OUT_ROWPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_C * 4 + OUT_COLPAIR: splitk_reduce<T, MXG_C, OUT_COLPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_Z * 4 + OUT_RE_ONLY: splitk_reduce<T, MXG_Z, OUT_RE_ONLY><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_Z * 4 + OUT_ROWPAIR: splitk_reduce<T, MXG_Z, OUT_ROWPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    case MXG_Z * 4 + OUT_COLPAIR: splitk_reduce<T, MXG_Z, OUT_COLPAIR><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto M) {
+    splitk_reduce<T, decltype(C)::value, decltype(M)::value><<<blocks, 256, 0, s>>>(ws, splits, Mp, Np, e);
+  });
+  return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gemm_splitk(int method, int c_dt, int mode, const GemmArgs& g, int splits, int64_t kslice,
@@ -392,14 +353,11 @@ cudaError_t launch_scale_c(const EpiArgs& e, int c_dt, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  switch (c_dt) {
-    case MXG_S: scale_c_kernel<MXG_S><<<static_cast<unsigned>(blocks), 256, 0, s>>>(e); break;
-    case MXG_D: scale_c_kernel<MXG_D><<<static_cast<unsigned>(blocks), 256, 0, s>>>(e); break;
-    case MXG_C: scale_c_kernel<MXG_C><<<static_cast<unsigned>(blocks), 256, 0, s>>>(e); break;
-    case MXG_Z: scale_c_kernel<MXG_Z><<<static_cast<unsigned>(blocks), 256, 0, s>>>(e); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  const int mode = (c_dt == MXG_C || c_dt == MXG_Z || c_dt == MXG_K || c_dt == MXG_W) ? OUT_ROWPAIR : OUT_REAL;
+  const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto) {
+    scale_c_kernel<decltype(C)::value><<<static_cast<unsigned>(blocks), 256, 0, s>>>(e);
+  });
+  return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
 }  // namespace mxg

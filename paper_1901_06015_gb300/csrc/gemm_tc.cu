@@ -31,19 +31,32 @@ namespace mxg {
 struct TcArgs {
   int64_t Mp, Np, Kp;   // padded real problem (multiples of 128, 256, BK)
   EpiArgs e;
+  int cdt, mode;        // C datatype and output mode (epilogue dispatched at run time)
   int* err;             // device error word set on a wait timeout (may be null)
 };
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4, TC_GM = 16;
+constexpr int TC_BM = 128, TC_BN = 256, TC_GM = 16;
 constexpr uint32_t ROWB = 64;                              // bytes of K per tile row (64-byte swizzle)
 constexpr uint32_t TILE_A = TC_BM * ROWB;                  // 8 KB
 constexpr uint32_t TILE_B = TC_BN * ROWB;                  // 16 KB
-constexpr uint32_t STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // A_hi, A_lo, B_hi, B_lo: 48 KB
-constexpr uint32_t NBARS = 2 * TC_STAGES + 2 + 2 + 1;      // full, empty, acc_full, acc_empty, drain
-constexpr uint32_t TC_SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t RING_BYTES = 192 * 1024;                // shared-memory ring
+constexpr uint32_t TC_SMEM = RING_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 2 * TC_BN;                  // two accumulators
+
+// Operand formats: the split forms load hi and lo planes of A and B and issue three
+// MMAs per k-step; TC16 loads one plane each and issues one.
+template <int SPLIT> struct TcFmt {
+  static constexpr int planes = (SPLIT == SPLIT_F16_ONE || SPLIT == SPLIT_BF16_ONE) ? 1 : 2;
+  static constexpr int elem = (SPLIT == SPLIT_TF32) ? 4 : 2;
+  // instruction-descriptor format code: 0 F16, 1 BF16 (kind::f16), 2 TF32 (kind::tf32)
+  static constexpr uint32_t fmt = (SPLIT == SPLIT_TF32) ? 2u : (SPLIT == SPLIT_F16_ONE ? 0u : 1u);
+  static_assert(fmt <= 2u, "format code");
+  static constexpr uint32_t stage_bytes = planes * (TILE_A + TILE_B);
+  static constexpr int stages = static_cast<int>(RING_BYTES / stage_bytes);   // 4 split, 8 TC16
+};
+constexpr uint32_t NBARS_MAX = 2 * 8 + 2 + 2 + 1;          // full, empty, acc_full, acc_empty, drain
 constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -121,8 +134,8 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
 
 template <int SPLIT>
 __device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-  if constexpr (SPLIT == SPLIT_BF16) {
-    constexpr uint32_t idesc = make_idesc(1, TC_BM, TC_BN);
+  if constexpr (SPLIT != SPLIT_TF32) {
+    constexpr uint32_t idesc = make_idesc(TcFmt<SPLIT>::fmt, TC_BM, TC_BN);
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
@@ -163,19 +176,47 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   *tn = r / gsz;
 }
 
-template <int SPLIT, int CDT, int MODE>
+// Epilogue of one 32-column chunk of the accumulator (C datatype and mode fixed).
+template <int CDT, int MODE>
+__device__ __forceinline__ void tc_epi_chunk(const EpiArgs& e, int64_t row, int64_t col0, const uint32_t (&v)[32],
+                                             int lane) {
+  if constexpr (MODE == OUT_ROWPAIR) {
+    // rows 2i and 2i+1 sit in lanes 2l and 2l+1: the even lane takes even columns,
+    // the odd lane odd columns
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const float mine = __uint_as_float(v[jj]);
+      const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+      if ((jj & 1) == (lane & 1)) {
+        const float pr = (lane & 1) ? other : mine, pi = (lane & 1) ? mine : other;
+        epi_store<float, CDT, MODE>(e, row >> 1, col0 + jj, pr, pi);
+      }
+    }
+  } else if constexpr (MODE == OUT_COLPAIR) {
+#pragma unroll
+    for (int jj = 0; jj < 32; jj += 2)
+      epi_store<float, CDT, MODE>(e, row, (col0 + jj) >> 1, __uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) epi_store<float, CDT, MODE>(e, row, col0 + jj, __uint_as_float(v[jj]), 0.0f);
+  }
+}
+
+template <int SPLIT>
 __global__ void __launch_bounds__(192, 1)
 tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
-  constexpr int ELEM = (SPLIT == SPLIT_BF16) ? 2 : 4;
-  constexpr int BK = ROWB / ELEM;           // k elements per 64-byte row
+  using F = TcFmt<SPLIT>;
+  constexpr int TC_STAGES = F::stages;
+  constexpr uint32_t STAGE_BYTES = F::stage_bytes;
+  constexpr int BK = ROWB / F::elem;        // k elements per 64-byte row
   constexpr int KSTEPS = ROWB / 32;         // MMAs per row (each consumes 32 bytes of K)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gen_base = smem_raw + (base - raw);
   const uint32_t bars = base + TC_STAGES * STAGE_BYTES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * STAGE_BYTES + 8 * NBARS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * STAGE_BYTES + 8 * NBARS_MAX);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (TC_STAGES + s); };
@@ -188,6 +229,7 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   const int ntiles = tiles_m * tiles_n;
   const int nkb = static_cast<int>(g.Kp / BK);
 
+  static_assert(2 * TC_STAGES + 5 <= static_cast<int>(NBARS_MAX), "barrier area");
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(full(s), 1);
@@ -231,10 +273,11 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           const uint32_t st = base + s * STAGE_BYTES;
           mbar_expect_tx(full(s), STAGE_BYTES);
           const int32_t kx = kb * BK;
+          // stage layout: A planes (F::planes x TILE_A), then B planes
           tma_load_2d(st, &mAh, kx, ym, full(s));
-          tma_load_2d(st + TILE_A, &mAl, kx, ym, full(s));
-          tma_load_2d(st + 2 * TILE_A, &mBh, kx, yn, full(s));
-          tma_load_2d(st + 2 * TILE_A + TILE_B, &mBl, kx, yn, full(s));
+          if constexpr (F::planes == 2) tma_load_2d(st + TILE_A, &mAl, kx, ym, full(s));
+          tma_load_2d(st + F::planes * TILE_A, &mBh, kx, yn, full(s));
+          if constexpr (F::planes == 2) tma_load_2d(st + 2 * TILE_A + TILE_B, &mBl, kx, yn, full(s));
         }
       }
       if (!ok) {
@@ -259,14 +302,16 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t st = base + s * STAGE_BYTES;
-          const uint32_t a_hi = st, a_lo = st + TILE_A, b_hi = st + 2 * TILE_A, b_lo = b_hi + TILE_B;
+          const uint32_t a_hi = st, a_lo = st + TILE_A, b_hi = st + F::planes * TILE_A, b_lo = b_hi + TILE_B;
 #pragma unroll
           for (int kk = 0; kk < KSTEPS; ++kk) {
             const uint32_t off = kk * 32;
             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
             mma_issue<SPLIT>(acc_tmem, sw64_desc(a_hi + off), sw64_desc(b_hi + off), first);
-            mma_issue<SPLIT>(acc_tmem, sw64_desc(a_hi + off), sw64_desc(b_lo + off), 1u);
-            mma_issue<SPLIT>(acc_tmem, sw64_desc(a_lo + off), sw64_desc(b_hi + off), 1u);
+            if constexpr (F::planes == 2) {
+              mma_issue<SPLIT>(acc_tmem, sw64_desc(a_hi + off), sw64_desc(b_lo + off), 1u);
+              mma_issue<SPLIT>(acc_tmem, sw64_desc(a_lo + off), sw64_desc(b_hi + off), 1u);
+            }
           }
           mma_commit(empty(s));
         }
@@ -299,27 +344,9 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       for (int c0 = 0; c0 < TC_BN; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-        if constexpr (MODE == OUT_ROWPAIR) {
-          // rows 2i and 2i+1 sit in lanes 2l and 2l+1: the even lane takes even
-          // columns, the odd lane odd columns
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const float mine = __uint_as_float(v[jj]);
-            const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-            if ((jj & 1) == (lane & 1)) {
-              const float pr = (lane & 1) ? other : mine, pi = (lane & 1) ? mine : other;
-              epi_store<float, CDT, MODE>(g.e, row >> 1, n0 + c0 + jj, pr, pi);
-            }
-          }
-        } else if constexpr (MODE == OUT_COLPAIR) {
-#pragma unroll
-          for (int jj = 0; jj < 32; jj += 2)
-            epi_store<float, CDT, MODE>(g.e, row, (n0 + c0 + jj) >> 1, __uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            epi_store<float, CDT, MODE>(g.e, row, n0 + c0 + jj, __uint_as_float(v[jj]), 0.0f);
-        }
+        with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
+          tc_epi_chunk<decltype(C)::value, decltype(M)::value>(g.e, row, n0 + c0, v, lane);
+        });
       }
       // release the accumulator to the MMA warp
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -373,53 +400,29 @@ bool get_encoder() {
 // 2-D map over a K-major plane (rows x Kp elements, row pitch Kp elements), box
 // (rows_box x 64 bytes), 64-byte swizzle.
 bool make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box) {
-  const int elem = (split == SPLIT_BF16) ? 2 : 4;
+  const int elem = (split == SPLIT_TF32) ? 4 : 2;
+  const CUtensorMapDataType dtype = (split == SPLIT_TF32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                    : (split == SPLIT_F16_ONE) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(rows)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * elem};
   const cuuint32_t box[2] = {static_cast<cuuint32_t>(ROWB / elem), rows_box};
   const cuuint32_t estr[2] = {1u, 1u};
-  const CUresult r = g_encode(map, split == SPLIT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                              2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const CUresult r = g_encode(map, dtype, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int SPLIT, int CDT, int MODE>
+template <int SPLIT>
 cudaError_t launch_one(const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
-  auto kern = tc_split_gemm<SPLIT, CDT, MODE>;
+  auto kern = tc_split_gemm<SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (g.Mp / TC_BM) * (g.Np / TC_BN);
   const int grid = static_cast<int>(ntiles < g_num_sms ? ntiles : g_num_sms);
   kern<<<grid, 192, TC_SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], g);
   return cudaGetLastError();
-}
-
-template <int SPLIT, int CDT>
-cudaError_t launch_mode(int mode, const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
-  constexpr bool cplx = CStore<CDT>::cplx;
-  if (!cplx) {
-    if (mode != OUT_REAL) return cudaErrorInvalidValue;
-    return launch_one<SPLIT, CDT, OUT_REAL>(maps, g, s);
-  }
-  switch (mode) {
-    case OUT_RE_ONLY: return launch_one<SPLIT, CDT, (cplx ? OUT_RE_ONLY : OUT_REAL)>(maps, g, s);
-    case OUT_ROWPAIR: return launch_one<SPLIT, CDT, (cplx ? OUT_ROWPAIR : OUT_REAL)>(maps, g, s);
-    case OUT_COLPAIR: return launch_one<SPLIT, CDT, (cplx ? OUT_COLPAIR : OUT_REAL)>(maps, g, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int SPLIT>
-cudaError_t launch_split(int c_dt, int mode, const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
-  switch (c_dt) {
-    case MXG_S: return launch_mode<SPLIT, MXG_S>(mode, maps, g, s);
-    case MXG_D: return launch_mode<SPLIT, MXG_D>(mode, maps, g, s);
-    case MXG_C: return launch_mode<SPLIT, MXG_C>(mode, maps, g, s);
-    case MXG_Z: return launch_mode<SPLIT, MXG_Z>(mode, maps, g, s);
-  }
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -430,11 +433,11 @@ cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s) 
 }
 
 // planes: A_hi, A_lo (Mp x Kp, K-major), B_hi, B_lo (Np x Kp, K-major)
-cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,
-                           int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s) {
+cudaError_t launch_gemm_tc(int method, int split, int c_dt, int mode, const void* const planes[4], int64_t Mp,
+                           int64_t Np, int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s) {
   if (!get_encoder()) return cudaErrorNotSupported;
-  const int split = (method == MXG_METHOD_BF16X3) ? SPLIT_BF16 : SPLIT_TF32;
-  const int bk = static_cast<int>(ROWB) / (split == SPLIT_BF16 ? 2 : 4);
+  (void)method;
+  const int bk = static_cast<int>(ROWB) / (split == SPLIT_TF32 ? 4 : 2);
   if (Mp % TC_BM || Np % TC_BN || Kp % bk) return cudaErrorInvalidValue;
   if ((Mp / TC_BM) * (Np / TC_BN) > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (Mp == 0 || Np == 0) return cudaSuccess;
@@ -448,9 +451,17 @@ cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const pla
   if (!make_map(&maps[0], planes[0], split, Mp, Kp, TC_BM) || !make_map(&maps[1], planes[1], split, Mp, Kp, TC_BM) ||
       !make_map(&maps[2], planes[2], split, Np, Kp, TC_BN) || !make_map(&maps[3], planes[3], split, Np, Kp, TC_BN))
     return cudaErrorInvalidValue;
-  TcArgs g{Mp, Np, Kp, e, err};
-  return split == SPLIT_BF16 ? launch_split<SPLIT_BF16>(c_dt, mode, maps, g, s)
-                             : launch_split<SPLIT_TF32>(c_dt, mode, maps, g, s);
+  TcArgs g{Mp, Np, Kp, e, c_dt, mode, err};
+  bool valid = false;
+  with_c_mode(c_dt, mode, [&](auto, auto) { valid = true; });
+  if (!valid) return cudaErrorInvalidValue;
+  switch (split) {
+    case SPLIT_TF32: return launch_one<SPLIT_TF32>(maps, g, s);
+    case SPLIT_BF16: return launch_one<SPLIT_BF16>(maps, g, s);
+    case SPLIT_F16_ONE: return launch_one<SPLIT_F16_ONE>(maps, g, s);
+    case SPLIT_BF16_ONE: return launch_one<SPLIT_BF16_ONE>(maps, g, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace mxg

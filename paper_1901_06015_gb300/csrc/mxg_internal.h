@@ -42,8 +42,9 @@ enum OutMode : int { OUT_REAL = 0, OUT_RE_ONLY = 1, OUT_ROWPAIR = 2, OUT_COLPAIR
 // kernels, K-major (element (kk, mm) at mm*ld + kk) for the tensor-core kernels.
 enum PackLayout : int { LAYOUT_MN_MAJOR = 0, LAYOUT_K_MAJOR = 1 };
 
-// Split formats written by the pack for the split-precision tensor-core methods.
-enum SplitKind : int { SPLIT_NONE = 0, SPLIT_TF32 = 1, SPLIT_BF16 = 2 };
+// Formats of the K-major planes written for the tensor-core methods: hi and lo planes
+// of the split forms, or one plane rounded to binary16 / bfloat16 (TC16).
+enum SplitKind : int { SPLIT_NONE = 0, SPLIT_TF32 = 1, SPLIT_BF16 = 2, SPLIT_F16_ONE = 3, SPLIT_BF16_ONE = 4 };
 
 struct PackArgs {
   const void* src;   // source operand, storage datatype src_dt
@@ -94,8 +95,9 @@ cudaError_t launch_gemm_splitk(int method, int c_dt, int mode, const GemmArgs& g
                                void* ws, cudaStream_t s);
 // Bounded-wait self-test: a wait nothing will satisfy, limited to `seconds`.
 cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s);
-// Split-precision tensor-core contraction: planes = {A_hi, A_lo, B_hi, B_lo}, K-major.
-cudaError_t launch_gemm_tc(int method, int c_dt, int mode, const void* const planes[4], int64_t Mp,
+// Tensor-core contraction: planes = {A_hi, A_lo, B_hi, B_lo}, K-major (one plane per
+// operand for the TC16 formats: the lo entries are ignored).
+cudaError_t launch_gemm_tc(int method, int split, int c_dt, int mode, const void* const planes[4], int64_t Mp,
                            int64_t Np, int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s);
 
 }  // namespace mxg

@@ -12,6 +12,9 @@
 // operand's contiguous dimension, so both sides are coalesced for row-, column- and
 // (as far as possible) general storage.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "mxg_internal.h"
 #include "../../include/mxgemm.h"
@@ -23,6 +26,22 @@ template <int DT> struct SrcT { using T = float; static constexpr bool cplx = fa
 template <> struct SrcT<MXG_D> { using T = double; static constexpr bool cplx = false; };
 template <> struct SrcT<MXG_C> { using T = float; static constexpr bool cplx = true; };
 template <> struct SrcT<MXG_Z> { using T = double; static constexpr bool cplx = true; };
+template <> struct SrcT<MXG_H> { using T = __half; static constexpr bool cplx = false; };
+template <> struct SrcT<MXG_K> { using T = __half; static constexpr bool cplx = true; };
+template <> struct SrcT<MXG_B> { using T = __nv_bfloat16; static constexpr bool cplx = false; };
+template <> struct SrcT<MXG_W> { using T = __nv_bfloat16; static constexpr bool cplx = true; };
+
+// Exact widening of a stored component to the working type.
+template <typename DT> __device__ __forceinline__ DT widen(float x) { return static_cast<DT>(x); }
+template <typename DT> __device__ __forceinline__ DT widen(double x) { return static_cast<DT>(x); }
+template <typename DT> __device__ __forceinline__ DT widen(__half x) { return static_cast<DT>(__half2float(x)); }
+template <typename DT> __device__ __forceinline__ DT widen(__nv_bfloat16 x) { return static_cast<DT>(__bfloat162float(x)); }
+
+// One rounding (RN-even) from the working type to binary16 / bfloat16.
+__device__ __forceinline__ __half to_f16(float x) { return __float2half_rn(x); }
+__device__ __forceinline__ __half to_f16(double x) { return __double2half(x); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(double x) { return __double2bfloat16(x); }
 
 // Round-to-nearest-even of an FP32 value to TF32 (10 explicit mantissa bits), done on
 // the bit pattern; infinities and NaNs pass through.
@@ -73,6 +92,8 @@ template <> struct OutVec<SPLIT_NONE, float> { static constexpr int n = 4; };
 template <> struct OutVec<SPLIT_NONE, double> { static constexpr int n = 2; };
 template <> struct OutVec<SPLIT_TF32, float> { static constexpr int n = 4; };
 template <> struct OutVec<SPLIT_BF16, float> { static constexpr int n = 8; };
+template <typename DT> struct OutVec<SPLIT_F16_ONE, DT> { static constexpr int n = 8; };
+template <typename DT> struct OutVec<SPLIT_BF16_ONE, DT> { static constexpr int n = 8; };
 
 // One 64 (mn) x 32 (p) tile of logical elements starting at (mn0, p0): read it with
 // the lanes along the source's unit-stride dimension (8 independent loads per
@@ -100,7 +121,7 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
     const int64_t mn = mn0 + lm, p = p0 + lp;
     lm_[i] = lm; lp_[i] = lp;
     in_[i] = (mn < a.MN && p < a.K);
-    vr_[i] = ST(0); vi_[i] = ST(0);
+    vr_[i] = ST(0.0f); vi_[i] = ST(0.0f);
     if (in_[i]) {
       const ST* sp = static_cast<const ST*>(a.src) + (mn * a.smn + p * a.sk) * (SC ? 2 : 1);
       vr_[i] = __ldg(sp);
@@ -109,9 +130,9 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    DT re = static_cast<DT>(vr_[i]);
+    DT re = widen<DT>(vr_[i]);
     if constexpr (SC) {   // a real source only ever uses the RE pattern
-      DT im = static_cast<DT>(vi_[i]);
+      DT im = widen<DT>(vi_[i]);
       if (a.conj) im = -im;
       if (a.fold) {       // alpha * x in the computation precision (literal complex alpha)
         const DT fr = static_cast<DT>(a.fold_re), fi = static_cast<DT>(a.fold_im);
@@ -149,6 +170,26 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
       const int64_t kk = p0 * fk + r0, mm = mn0 * fm + c;
       if (kk >= a.Kp || mm >= a.MNp) continue;
       const int lm = c / fm, tt = c - lm * fm;
+      const int64_t off = mm * a.ld + kk;
+      if constexpr (SPLIT == SPLIT_F16_ONE || SPLIT == SPLIT_BF16_ONE) {
+        // one plane rounded once from the working type (TC16)
+        uint4 pk;
+        uint16_t* p16 = reinterpret_cast<uint16_t*>(&pk);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+          const int r = r0 + u, lp = r / fk, s = r - lp * fk;
+          const DT x = SC ? pattern_value<DT>(a.pattern, s, tt, sm.re[lp][lm], sm.im[lp][lm]) : sm.re[lp][lm];
+          if constexpr (SPLIT == SPLIT_F16_ONE) {
+            const __half hv = to_f16(x);
+            p16[u] = *reinterpret_cast<const uint16_t*>(&hv);
+          } else {
+            const __nv_bfloat16 bv = to_bf16(x);
+            p16[u] = *reinterpret_cast<const uint16_t*>(&bv);
+          }
+        }
+        *reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.dst) + off) = pk;
+        continue;
+      } else {
       float hi[V], lo[V];
 #pragma unroll
       for (int u = 0; u < V; ++u) {
@@ -164,7 +205,6 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
           lo[u] = x - hi[u];
         }
       }
-      const int64_t off = mm * a.ld + kk;
       if constexpr (SPLIT == SPLIT_TF32) {
         *reinterpret_cast<float4*>(static_cast<float*>(a.dst) + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<float4*>(static_cast<float*>(a.dst_lo) + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
@@ -181,6 +221,7 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
         }
         *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst) + off) = ph;
         *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst_lo) + off) = pl;
+      }
       }
     }
   }
@@ -217,6 +258,10 @@ __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __res
     case MXG_D: pack_tile<MXG_D, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
     case MXG_C: pack_tile<MXG_C, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
     case MXG_Z: pack_tile<MXG_Z, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
+    case MXG_H: pack_tile<MXG_H, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
+    case MXG_K: pack_tile<MXG_K, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
+    case MXG_B: pack_tile<MXG_B, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
+    case MXG_W: pack_tile<MXG_W, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
   }
 }
 
@@ -234,6 +279,12 @@ cudaError_t launch_src(const PackArgs& a, int comp_double, cudaStream_t s) {
     pack_kernel<SDT, float, LAYOUT_K_MAJOR, SPLIT_TF32><<<grid, 256, 0, s>>>(a, ntp);
   } else if (a.split == SPLIT_BF16 && a.layout == LAYOUT_K_MAJOR && !comp_double) {
     pack_kernel<SDT, float, LAYOUT_K_MAJOR, SPLIT_BF16><<<grid, 256, 0, s>>>(a, ntp);
+  } else if ((a.split == SPLIT_F16_ONE || a.split == SPLIT_BF16_ONE) && a.layout == LAYOUT_K_MAJOR) {
+    // working type: the source's own precision, so the 16-bit rounding happens once
+    constexpr bool src_double = (SDT == MXG_D || SDT == MXG_Z);
+    using WT = typename std::conditional<src_double, double, float>::type;
+    if (a.split == SPLIT_F16_ONE) pack_kernel<SDT, WT, LAYOUT_K_MAJOR, SPLIT_F16_ONE><<<grid, 256, 0, s>>>(a, ntp);
+    else pack_kernel<SDT, WT, LAYOUT_K_MAJOR, SPLIT_BF16_ONE><<<grid, 256, 0, s>>>(a, ntp);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -262,6 +313,10 @@ cudaError_t launch_pack(const PackArgs& a, int comp_double, cudaStream_t s) {
     case MXG_D: return launch_src<MXG_D>(a, comp_double, s);
     case MXG_C: return launch_src<MXG_C>(a, comp_double, s);
     case MXG_Z: return launch_src<MXG_Z>(a, comp_double, s);
+    case MXG_H: return launch_src<MXG_H>(a, comp_double, s);
+    case MXG_K: return launch_src<MXG_K>(a, comp_double, s);
+    case MXG_B: return launch_src<MXG_B>(a, comp_double, s);
+    case MXG_W: return launch_src<MXG_W>(a, comp_double, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -28,6 +28,7 @@ struct Plan {
   Call work{};            // after the optional whole-op transpose
   int kind = PLAN_NOOP;
   int domain_case = 0;    // of the call as given (Fig. "mixeddom")
+  int comp = 0;                     // resolved MXG_PREC_* (S, D, H or B)
   bool comp_double = false;
   int method = 0;
   bool swapped = false;

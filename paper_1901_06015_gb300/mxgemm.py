@@ -11,10 +11,12 @@ import threading
 
 from . import build as _build
 
-DT_CODES = {"s": 0, "d": 1, "c": 2, "z": 3}
+# storage datatypes: s, d, c, z; h / k = binary16 real / complex; b / w = bfloat16
+# real / complex
+DT_CODES = {"s": 0, "d": 1, "c": 2, "z": 3, "h": 4, "k": 5, "b": 6, "w": 7}
 TRANS_CODES = {"n": 0, "t": 1, "c": 2, "h": 3}
-PREC_CODES = {"s": 0, "d": 1, "c": 2}  # 'c': the precision of C
-METHODS = {"auto": 0, "ffma": 1, "tf32x3": 2, "bf16x3": 3, "dmma": 4, "dfma": 5}
+PREC_CODES = {"s": 0, "d": 1, "c": 2, "h": 3, "b": 4}  # 'c': the precision of C
+METHODS = {"auto": 0, "ffma": 1, "tf32x3": 2, "bf16x3": 3, "dmma": 4, "dfma": 5, "tc16": 6}
 CASE_NAMES = ["0", "1b", "1a", "2ab", "1c", "2bc", "2ac", "3"]
 
 _i32, _i64, _dbl, _vp, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -140,22 +142,32 @@ def mxg_strerror(status):
 
 
 def dt_of(t):
+    """Storage datatype of a tensor. A 3-D float16 / bfloat16 tensor of shape
+    (rows, cols, 2) with unit last stride is a complex binary16 / bfloat16 matrix
+    (torch has no complex bfloat16)."""
     import torch
-    m = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
-    if t.dtype not in m:
-        raise TypeError(f"unsupported dtype {t.dtype}")
+    m = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z",
+         torch.float16: "h", torch.complex32: "k", torch.bfloat16: "b"}
+    if t.dim() == 3 and t.shape[2] == 2 and t.stride(2) == 1 and t.dtype in (torch.float16, torch.bfloat16):
+        return "k" if t.dtype == torch.float16 else "w"
+    if t.dim() != 2 or t.dtype not in m:
+        raise TypeError(f"unsupported matrix {tuple(t.shape)} of {t.dtype}")
     return m[t.dtype]
 
 
 def _mat(t):
-    if t.dim() != 2:
-        raise ValueError("matrices must be 2-D tensors")
+    dt = dt_of(t)
+    if t.dim() == 3:
+        rs, cs = t.stride(0), t.stride(1)
+        if rs % 2 or cs % 2:
+            raise ValueError("a (rows, cols, 2) complex matrix needs even row and column strides")
+        return ctypes.c_void_p(t.data_ptr()), DT_CODES[dt], int(rs // 2), int(cs // 2)
     rs, cs = t.stride()
-    return ctypes.c_void_p(t.data_ptr()), DT_CODES[dt_of(t)], int(rs), int(cs)
+    return ctypes.c_void_p(t.data_ptr()), DT_CODES[dt], int(rs), int(cs)
 
 
 def _dims(transa, transb, A, C):
-    m, n = C.shape
+    m, n = C.shape[0], C.shape[1]
     k = A.shape[0] if transa in ("t", "h") else A.shape[1]
     return int(m), int(n), int(k)
 

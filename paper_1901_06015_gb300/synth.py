@@ -136,8 +136,16 @@ def problem(seed, combo, m, n, k, dist="uniform", transa="n", transb="n",
 def torch_matrix(gen, rows, cols, dt, device, low=-1.0, high=1.0):
     """Device-side uniform matrix, column-major (stored as the transpose of a row-major
     cols x rows tensor). Used for the large benchmark inputs, which are checked
-    against the oracle on sampled blocks copied back to the host."""
+    against the oracle on sampled blocks copied back to the host. A complex 16-bit
+    matrix is a (rows, cols, 2) float16 / bfloat16 tensor."""
     import torch
+    if dt in ("h", "k", "b", "w"):
+        t16 = torch.float16 if dt in ("h", "k") else torch.bfloat16
+        ncomp = 2 if dt in ("k", "w") else 1
+        raw = torch.empty((cols, rows, ncomp), dtype=torch.float32, device=device)
+        raw.uniform_(low, high, generator=gen)
+        raw = raw.to(t16)
+        return raw.permute(1, 0, 2) if ncomp == 2 else raw[..., 0].t()
     tdt = {"s": torch.float32, "d": torch.float64,
            "c": torch.complex64, "z": torch.complex128}[dt]
     real = torch.float64 if dt in ("d", "z") else torch.float32

@@ -11,15 +11,18 @@ Re(A) when C and B are real, Re(B) when C and A are real, else the full operand.
 """
 import numpy as np
 
-U = {"s": 2.0 ** -24, "d": 2.0 ** -53}
+U = {"s": 2.0 ** -24, "d": 2.0 ** -53, "h": 2.0 ** -11, "b": 2.0 ** -8}
+# unit roundoff of the summation for each computation precision: the 16-bit precisions
+# round A and B to binary16 / bfloat16 (as the oracle does) and sum in FP32
+U_SUM = {"s": 2.0 ** -24, "d": 2.0 ** -53, "h": 2.0 ** -24, "b": 2.0 ** -24}
 
 
 def prec_of(dt):
-    return "d" if dt in ("d", "z") else "s"
+    return {"d": "d", "z": "d", "h": "h", "k": "h", "b": "b", "w": "b"}.get(dt, "s")
 
 
 def is_complex(dt):
-    return dt in ("c", "z")
+    return dt in ("c", "z", "k", "w")
 
 
 def comp_prec(combo):
@@ -28,7 +31,8 @@ def comp_prec(combo):
 
 
 def op(X, trans):
-    X = np.asarray(X).astype(np.complex128)
+    from paper_1901_06015_gb300 import synth
+    X = synth.to_c128(np.asarray(X))
     if trans in ("t", "h"):
         X = X.T
     if trans in ("c", "h"):
@@ -46,7 +50,7 @@ U_SPLIT = {"bf16x3": 3.0 * 2.0 ** -16 * (1 + 2.0 ** -7), "tf32x3": 3.0 * 2.0 ** 
 
 
 def tolerance(combo, k, method=None):
-    tol = 4.0 * max(k, 1) * U[comp_prec(combo)] + 4.0 * U[prec_of(combo[0])]
+    tol = 4.0 * max(k, 1) * U_SUM[comp_prec(combo)] + 4.0 * U[prec_of(combo[0])]
     return tol + U_SPLIT.get(method, 0.0)
 
 
@@ -63,7 +67,8 @@ def entering_norms(combo, A, B, transa="n", transb="n"):
 def normwise_error(combo, C_gpu, C_ref, A, B, C_in, alpha, beta, transa="n", transb="n"):
     """Return (err, bound-denominator) for C_gpu against the oracle's unrounded C_ref."""
     na, nb = entering_norms(combo, A, B, transa, transb)
-    den = abs(alpha) * na * nb + abs(beta) * float(np.linalg.norm(np.asarray(C_in).astype(np.complex128)))
-    diff = np.asarray(C_gpu).astype(np.complex128) - np.asarray(C_ref)
+    from paper_1901_06015_gb300 import synth
+    den = abs(alpha) * na * nb + abs(beta) * float(np.linalg.norm(synth.to_c128(np.asarray(C_in))))
+    diff = synth.to_c128(np.asarray(C_gpu)) - np.asarray(C_ref)
     num = float(np.linalg.norm(diff))
     return (num / den if den > 0 else num), den
