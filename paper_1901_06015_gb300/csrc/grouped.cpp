@@ -167,7 +167,7 @@ int tune_bucket(mxg_group_s* g, Bucket& b) {
   std::vector<size_t> off(b.probs.size());
   for (size_t i = 0; i < b.probs.size(); ++i) {
     const GroupProb& p = b.probs[i];
-    const size_t es = (p.cdt == MXG_S) ? 4 : (p.cdt == MXG_Z ? 16 : 8);
+    const size_t es = dt_bytes(p.cdt);
     off[i] = bytes;
     bytes += al256(static_cast<size_t>(p.e.m) * p.e.n * es);
   }
@@ -274,6 +274,8 @@ int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int metho
     // resolve the precision first, then plan with the bucket's padding method
     Plan probe;
     int st = make_plan(c, MXG_METHOD_AUTO, &probe);
+    // buckets are single and double precision; the 16-bit precisions run per call
+    if (st == MXG_OK && (probe.comp == MXG_PREC_H || probe.comp == MXG_PREC_B)) st = MXG_ENOTSUP;
     if (st == MXG_OK) st = make_plan(c, probe.comp_double ? bd.plan_method : bs.plan_method, &g->plans[i]);
     if (st == MXG_OK) {
       const Plan& P = g->plans[i];

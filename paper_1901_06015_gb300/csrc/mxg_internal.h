@@ -27,6 +27,12 @@ namespace mxg {
 //                                           for A, Eq. (2) for B)
 enum PackPattern : int { PAT_RE = 0, PAT_SPLIT_MN = 1, PAT_SPLIT_K = 2, PAT_ONE_E = 3 };
 
+// Bytes of one element of a storage datatype (MXG_S .. MXG_W).
+inline size_t dt_bytes(int dt) {
+  static const size_t b[8] = {4, 8, 8, 16, 2, 4, 2, 4};
+  return (dt >= 0 && dt < 8) ? b[dt] : 0;
+}
+
 __host__ __device__ inline int pat_fk(int p) { return (p == PAT_SPLIT_K || p == PAT_ONE_E) ? 2 : 1; }
 __host__ __device__ inline int pat_fm(int p) { return (p == PAT_SPLIT_MN || p == PAT_ONE_E) ? 2 : 1; }
 

@@ -65,7 +65,6 @@ class Arena {
   std::map<size_t, size_t> free_;
 };
 
-size_t dt_bytes(int dt) { return dt == MXG_S ? 4 : (dt == MXG_Z ? 16 : 8); }
 
 struct Req {
   uint64_t id = 0;

@@ -71,3 +71,34 @@ def test_16bit_sampled_blocks_4096(combo):
         got = from_device(C[i:i + BS, j:j + BS], combo[0])
         err, _ = normwise_error(combo, got, ref, Ap, Bp, C0, 1.0, 1.0)
         assert err <= tolerance(combo, N, "tc16"), (combo, (i, j), err)
+
+
+def test_16bit_storage_in_grouped_and_served_forms():
+    """16-bit storage with single/double computation runs in a grouped launch; a 16-bit
+    computation precision is served (per call) but not grouped (MXG_ENOTSUP)."""
+    import paper_1901_06015_gb300 as mx
+    combos = ["hsss", "sbbs", "kkcd", "wzwd", "hhhs", "bdbd"]
+    probs = [synth.problem(40 + i, c, 50 + 7 * i, 40, 60) for i, c in enumerate(combos)]
+    dev = [(to_device(A), to_device(B), to_device(C)) for (A, B, C) in probs]
+    items = [("n", "n", 1.5, dA, dB, -0.5, dC, c[3]) for c, (dA, dB, dC) in zip(combos, dev)]
+    g = mx.Group(items, tune=True, graph=True)
+    g.run()
+    torch.cuda.synchronize()
+    for c, (A, B, C0), (_, _, dC) in zip(combos, probs, dev):
+        ref = oracle_mxgemm("n", "n", 1.5, A, B, -0.5, C0.copy(), comp=c[3])
+        err, _ = normwise_error(c, from_device(dC, c[0]), ref, A, B, C0, 1.5, -0.5)
+        assert err <= tolerance(c, 60), (c, err)
+    g.close()
+    A, B, C0 = synth.problem(50, "hhhh", 30, 20, 40)
+    with pytest.raises(mx.MxgError) as e:
+        mx.Group([("n", "n", 1.0, to_device(A), to_device(B), 0.0, to_device(C0), "h")], tune=False, graph=False)
+    assert e.value.status == 6
+    srv = mx.Server(n_streams=2, hbm_budget_bytes=1 << 28)
+    dA, dB, dC = to_device(A), to_device(B), to_device(C0)
+    srv.submit(("n", "n", 1.0, dA, dB, 0.0, dC, "h"))
+    srv.drain(30)
+    assert srv.poll()[0]["status"] == 0
+    srv.close()
+    ref = oracle_mxgemm("n", "n", 1.0, A, B, 0.0, C0.copy(), comp="h")
+    err, _ = normwise_error("hhhh", from_device(dC, "h"), ref, A, B, C0, 1.0, 0.0)
+    assert err <= tolerance("hhhh", 40, "tc16")
