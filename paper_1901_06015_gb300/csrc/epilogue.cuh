@@ -72,12 +72,32 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_ct<__nv_bfloat16>(float 
 template <> __device__ __forceinline__ __nv_bfloat16 to_ct<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
 
 
+// C's value at (i, j) before the update, in C's storage type (im = 0 for a real C);
+// zero, and not read, where beta == 0 or (i, j) lies outside C. The kernels read a
+// thread's group of C elements with epi_load first and then update them with
+// epi_update, so that the group's loads are in flight together rather than one
+// load-update-store after another.
+template <int CDT> struct COld { typename CStore<CDT>::T re, im; };
+
+template <int CDT>
+__device__ __forceinline__ COld<CDT> epi_load(const EpiArgs& e, int64_t i, int64_t j) {
+  using CT = typename CStore<CDT>::T;
+  COld<CDT> o{to_ct<CT>(0.0f), to_ct<CT>(0.0f)};
+  if (e.beta_zero || i >= e.m || j >= e.n) return o;
+  const CT* c = static_cast<const CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
+  o.re = c[0];
+  if constexpr (CStore<CDT>::cplx) o.im = c[1];
+  return o;
+}
+
 // Update C(i, j) with the product value (pr, pi), both in the computation precision
-// AccT. pi is ignored unless MODE pairs two real results into one complex value.
-// Order of operations (Sec. 7.1): t = alpha*P rounded in AccT, cast to C's precision;
-// beta*C formed in C's precision; their sum rounded in C's precision.
+// AccT, given C's old value from epi_load. pi is ignored unless MODE pairs two real
+// results into one complex value. Order of operations (Sec. 7.1): t = alpha*P rounded
+// in AccT, cast to C's precision; beta*C formed in C's precision; their sum rounded in
+// C's precision.
 template <typename AccT, int CDT, int MODE>
-__device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j, AccT pr, AccT pi) {
+__device__ __forceinline__ void epi_update(const EpiArgs& e, int64_t i, int64_t j, AccT pr, AccT pi,
+                                           const COld<CDT>& old) {
   using CT = typename CStore<CDT>::T;
   if (i >= e.m || j >= e.n) return;
   const AccT ar = static_cast<AccT>(e.ar);
@@ -85,7 +105,7 @@ __device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j
   if constexpr (!CStore<CDT>::cplx) {
     // C real: alpha and beta projected onto the real line (Sec. 7.2).
     const CT t = to_ct<CT>(mul_rn(ar, pr));
-    c[0] = e.beta_zero ? t : add_rn(mul_rn(to_ct<CT>(e.br), c[0]), t);
+    c[0] = e.beta_zero ? t : add_rn(mul_rn(to_ct<CT>(e.br), old.re), t);
   } else {
     AccT tr, ti;
     const AccT ai_ = static_cast<AccT>(e.ai);
@@ -103,13 +123,19 @@ __device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j
       c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? to_ct<CT>(0.0f) : tci;
     } else {
       const CT br = to_ct<CT>(e.br), bi = to_ct<CT>(e.bi);
-      const CT cr = c[0], ci = c[1];
+      const CT cr = old.re, ci = old.im;
       const CT bcr = sub_rn(mul_rn(br, cr), mul_rn(bi, ci));
       const CT bci = add_rn(mul_rn(br, ci), mul_rn(bi, cr));
       c[0] = add_rn(bcr, tcr);
       c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? bci : add_rn(bci, tci);
     }
   }
+}
+
+// Load, update and store one element of C.
+template <typename AccT, int CDT, int MODE>
+__device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j, AccT pr, AccT pi) {
+  epi_update<AccT, CDT, MODE>(e, i, j, pr, pi, epi_load<CDT>(e, i, j));
 }
 
 }  // namespace mxg

@@ -94,23 +94,40 @@ __device__ __forceinline__ void dmma_stage(double* smem, const double (&acc)[4][
   __syncthreads();
 }
 
+// Each thread updates elements tid, tid + 128, ... of the tile's output grid, eight at
+// a time: the eight C loads first, then the updates.
 template <int CDT, int MODE>
 __device__ __forceinline__ void dmma_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const double* Cs) {
-  const int tid = threadIdx.x;
-  if constexpr (MODE == OUT_ROWPAIR) {
-    for (int idx = tid; idx < (DM_T / 2) * DM_T; idx += 128) {
+  constexpr int NOUT = (MODE == OUT_ROWPAIR || MODE == OUT_COLPAIR) ? DM_T * DM_T / 2 : DM_T * DM_T;
+  constexpr int B = 8;
+  static_assert(NOUT % (128 * B) == 0, "whole batches per thread");
+  auto where = [&](int idx, int64_t* i, int64_t* j, int* o_r, int* o_i) {
+    if constexpr (MODE == OUT_ROWPAIR) {
       const int rp = idx % (DM_T / 2), col = idx / (DM_T / 2);
-      epi_store<double, CDT, MODE>(e, (m0 >> 1) + rp, n0 + col, Cs[col * DM_CLD + 2 * rp], Cs[col * DM_CLD + 2 * rp + 1]);
-    }
-  } else if constexpr (MODE == OUT_COLPAIR) {
-    for (int idx = tid; idx < DM_T * (DM_T / 2); idx += 128) {
+      *i = (m0 >> 1) + rp; *j = n0 + col; *o_r = col * DM_CLD + 2 * rp; *o_i = *o_r + 1;
+    } else if constexpr (MODE == OUT_COLPAIR) {
       const int row = idx % DM_T, cp = idx / DM_T;
-      epi_store<double, CDT, MODE>(e, m0 + row, (n0 >> 1) + cp, Cs[2 * cp * DM_CLD + row], Cs[(2 * cp + 1) * DM_CLD + row]);
-    }
-  } else {
-    for (int idx = tid; idx < DM_T * DM_T; idx += 128) {
+      *i = m0 + row; *j = (n0 >> 1) + cp; *o_r = 2 * cp * DM_CLD + row; *o_i = *o_r + DM_CLD;
+    } else {
       const int row = idx % DM_T, col = idx / DM_T;
-      epi_store<double, CDT, MODE>(e, m0 + row, n0 + col, Cs[col * DM_CLD + row], 0.0);
+      *i = m0 + row; *j = n0 + col; *o_r = col * DM_CLD + row; *o_i = -1;
+    }
+  };
+  for (int base = threadIdx.x; base < NOUT; base += 128 * B) {
+    COld<CDT> old[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      int64_t i, j;
+      int o_r, o_i;
+      where(base + 128 * u, &i, &j, &o_r, &o_i);
+      old[u] = epi_load<CDT>(e, i, j);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      int64_t i, j;
+      int o_r, o_i;
+      where(base + 128 * u, &i, &j, &o_r, &o_i);
+      epi_update<double, CDT, MODE>(e, i, j, Cs[o_r], o_i >= 0 ? Cs[o_i] : 0.0, old[u]);
     }
   }
 }

@@ -126,23 +126,42 @@ __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int6
   const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
   auto row_of = [&](int i) -> int64_t { return m0 + (i < H ? tm * H + i : TM / 2 + tm * H + (i - H)); };
   auto col_of = [&](int j) -> int64_t { return n0 + (j < H ? tn * H + j : TM / 2 + tn * H + (j - H)); };
+  // H elements of one row (or row pair) of the thread's block at a time: their C loads
+  // first, then the updates
   if constexpr (MODE == OUT_ROWPAIR) {
 #pragma unroll
     for (int i = 0; i < R; i += 2)
 #pragma unroll
-      for (int j = 0; j < R; ++j)
-        epi_store<T, CDT, MODE>(e, row_of(i) >> 1, col_of(j), acc[i][j], acc[i + 1][j]);
+      for (int j0 = 0; j0 < R; j0 += H) {
+        COld<CDT> old[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) old[j] = epi_load<CDT>(e, row_of(i) >> 1, col_of(j0 + j));
+#pragma unroll
+        for (int j = 0; j < H; ++j)
+          epi_update<T, CDT, MODE>(e, row_of(i) >> 1, col_of(j0 + j), acc[i][j0 + j], acc[i + 1][j0 + j], old[j]);
+      }
   } else if constexpr (MODE == OUT_COLPAIR) {
 #pragma unroll
-    for (int i = 0; i < R; ++i)
+    for (int i = 0; i < R; ++i) {
+      COld<CDT> old[H];
+#pragma unroll
+      for (int j = 0; j < R; j += 2) old[j / 2] = epi_load<CDT>(e, row_of(i), col_of(j) >> 1);
 #pragma unroll
       for (int j = 0; j < R; j += 2)
-        epi_store<T, CDT, MODE>(e, row_of(i), col_of(j) >> 1, acc[i][j], acc[i][j + 1]);
+        epi_update<T, CDT, MODE>(e, row_of(i), col_of(j) >> 1, acc[i][j], acc[i][j + 1], old[j / 2]);
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < R; ++j) epi_store<T, CDT, MODE>(e, row_of(i), col_of(j), acc[i][j], T(0));
+      for (int j0 = 0; j0 < R; j0 += H) {
+        COld<CDT> old[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) old[j] = epi_load<CDT>(e, row_of(i), col_of(j0 + j));
+#pragma unroll
+        for (int j = 0; j < H; ++j)
+          epi_update<T, CDT, MODE>(e, row_of(i), col_of(j0 + j), acc[i][j0 + j], T(0), old[j]);
+      }
   }
 }
 

@@ -176,29 +176,53 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   *tn = r / gsz;
 }
 
-// Epilogue of one 32-column chunk of the accumulator (C datatype and mode fixed).
+// Epilogue of one 32-column chunk of the accumulator (C datatype and mode fixed), in
+// two phases: tc_epi_load reads the thread's old C values for the chunk (all loads in
+// flight together, overlapping the TMEM read), tc_epi_finish updates and stores them.
+// ROWPAIR: rows 2i and 2i+1 (real and imaginary parts) sit in lanes 2l and 2l+1; the
+// even lane updates the even columns of the chunk, the odd lane the odd ones. COLPAIR: columns 2j, 2j+1 form one
+// complex column.
+template <int MODE> struct TcChunk { static constexpr int nold = (MODE == OUT_ROWPAIR || MODE == OUT_COLPAIR) ? 16 : 32; };
+
 template <int CDT, int MODE>
-__device__ __forceinline__ void tc_epi_chunk(const EpiArgs& e, int64_t row, int64_t col0, const uint32_t (&v)[32],
-                                             int lane) {
+__device__ __forceinline__ void tc_epi_load(const EpiArgs& e, int64_t row, int64_t col0, int lane,
+                                            COld<CDT> (&old)[TcChunk<MODE>::nold]) {
   if constexpr (MODE == OUT_ROWPAIR) {
-    // rows 2i and 2i+1 sit in lanes 2l and 2l+1: the even lane takes even columns,
-    // the odd lane odd columns
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-      const float mine = __uint_as_float(v[jj]);
-      const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-      if ((jj & 1) == (lane & 1)) {
-        const float pr = (lane & 1) ? other : mine, pi = (lane & 1) ? mine : other;
-        epi_store<float, CDT, MODE>(e, row >> 1, col0 + jj, pr, pi);
-      }
+    for (int t = 0; t < 16; ++t) old[t] = epi_load<CDT>(e, row >> 1, col0 + 2 * t + (lane & 1));
+  } else if constexpr (MODE == OUT_COLPAIR) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) old[t] = epi_load<CDT>(e, row, (col0 >> 1) + t);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) old[jj] = epi_load<CDT>(e, row, col0 + jj);
+  }
+}
+
+template <int CDT, int MODE>
+__device__ __forceinline__ void tc_epi_finish(const EpiArgs& e, int64_t row, int64_t col0, const uint32_t (&v)[32],
+                                              int lane, const COld<CDT> (&old)[TcChunk<MODE>::nold]) {
+  if constexpr (MODE == OUT_ROWPAIR) {
+    // per column pair (2t, 2t+1) one exchange: the even lane sends its value of column
+    // 2t+1 and receives the odd lane's value of column 2t, so both lanes of the pair
+    // update one element (no divergence)
+    const bool odd = (lane & 1) != 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const float ve = __uint_as_float(v[2 * t]), vo = __uint_as_float(v[2 * t + 1]);
+      const float got = __shfl_xor_sync(0xffffffffu, odd ? ve : vo, 1);
+      const float pr = odd ? got : ve, pi = odd ? vo : got;
+      epi_update<float, CDT, MODE>(e, row >> 1, col0 + 2 * t + (odd ? 1 : 0), pr, pi, old[t]);
     }
   } else if constexpr (MODE == OUT_COLPAIR) {
 #pragma unroll
-    for (int jj = 0; jj < 32; jj += 2)
-      epi_store<float, CDT, MODE>(e, row, (col0 + jj) >> 1, __uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+    for (int t = 0; t < 16; ++t)
+      epi_update<float, CDT, MODE>(e, row, (col0 >> 1) + t, __uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]),
+                                   old[t]);
   } else {
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj) epi_store<float, CDT, MODE>(e, row, col0 + jj, __uint_as_float(v[jj]), 0.0f);
+    for (int jj = 0; jj < 32; ++jj)
+      epi_update<float, CDT, MODE>(e, row, col0 + jj, __uint_as_float(v[jj]), 0.0f, old[jj]);
   }
 }
 
@@ -340,14 +364,17 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       const int64_t m0 = static_cast<int64_t>(tm) * TC_BM, n0 = static_cast<int64_t>(tn) * TC_BN;
       const int64_t row = m0 + 32 * q + lane;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b * TC_BN);
+      with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
+        constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
 #pragma unroll 1
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-        with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
-          tc_epi_chunk<decltype(C)::value, decltype(M)::value>(g.e, row, n0 + c0, v, lane);
-        });
-      }
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          COld<CDT> old[TcChunk<MODE>::nold];
+          tc_epi_load<CDT, MODE>(g.e, row, n0 + c0, lane, old);
+          uint32_t v[32];
+          tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
+          tc_epi_finish<CDT, MODE>(g.e, row, n0 + c0, v, lane, old);
+        }
+      });
       // release the accumulator to the MMA warp
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
