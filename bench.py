@@ -29,6 +29,12 @@ CASES = list(itertools.product([0, 1], repeat=3))           # (C, A, B) complex?
 PATTERNS = list(itertools.product("sd", repeat=3))           # (C, A, B) precision
 R_OF = {(0, 0, 0): 1, (0, 0, 1): 1, (0, 1, 0): 1, (0, 1, 1): 2,
         (1, 0, 0): 1, (1, 0, 1): 2, (1, 1, 0): 2, (1, 1, 1): 4}
+
+
+def real_products(combo):
+    """R of the domain case of combo (C, A, B datatypes, then the computation precision)."""
+    from paper_1901_06015_gb300.synth import is_complex
+    return R_OF[tuple(int(is_complex(dt)) for dt in combo[:3])]
 NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
 
@@ -429,7 +435,7 @@ def run_precision(args):
             for combo in PRECISION_COMBOS:
                 gen.manual_seed(precision_seed(combo, n, dist))
                 A, B, C0 = precision_inputs(gen, combo, n, dist, dev)
-                R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+                R = real_products(combo)
                 for meth in methods:
                     C = C0.clone()
                     mx.mxgemm_ex(h, meth, "n", "n", 1.0, A, B, 1.0, C, comp="s")   # warm
@@ -482,7 +488,7 @@ def grouped_problems(count, seed, lo, hi, dev):
         B = synth.torch_matrix(gen, k, n, combo[2], dev)
         C = synth.torch_matrix(gen, m, n, combo[0], dev)
         items.append(("n", "n", 1.5, A, B, -0.5, C, combo[3]))
-        R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+        R = real_products(combo)
         flops += 2.0 * m * n * k * R
     return items, flops
 
@@ -564,7 +570,7 @@ def run_serving(args):
         combo = combos[int(rng.integers(len(combos)))]
         m, n, k = (int(round(float(np.exp(rng.uniform(np.log(32), np.log(4096)))))) for _ in range(3))
         al, be = float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2))
-        R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+        R = real_products(combo)
         reqs.append((combo, m, n, k, al, be, 2.0 * m * n * k * R))
     total_flops = sum(r[6] for r in reqs)
 
@@ -666,7 +672,7 @@ def run_single(args):
     C = operand(combo[0], lc, mm, nn)
     h = mx.Handle(); h.set_stream(stream)
     h.set_split_k(args.split_k)
-    R = R_OF[(int(combo[0] in "cz"), int(combo[1] in "cz"), int(combo[2] in "cz"))]
+    R = real_products(combo)
     times = []
     h.set_phase_timing(True)
     for i in range(args.warmup + args.reps):

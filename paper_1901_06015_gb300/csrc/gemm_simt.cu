@@ -5,8 +5,11 @@
 //
 //  * simt tiles (FFMA for float, DFMA for double): 256 threads as 16 x 16, tile
 //    32H x 32H x 8, each thread 2H x 2H outputs, H = elements per vector load
-//    (float: H = 4 -> 128 x 128 or H = 2 -> 64 x 64; double: H = 2 -> 64 x 64).
-//    H must be even: the complex epilogue pairs a thread's rows 2i, 2i+1 (or columns).
+//    (float: H = 4 -> 128 x 128, H = 2 -> 64 x 64, H = 1 -> 32 x 32; double: H = 2 ->
+//    64 x 64, H = 1 -> 32 x 32). With H >= 2 a thread's rows are two runs of H at
+//    t*H and 16H + t*H; with H = 1 they are the adjacent pair 2t, 2t+1. Either way a
+//    thread holds whole row pairs 2i, 2i+1 (and column pairs), which the complex
+//    epilogue combines.
 //  (The FP64 tensor-core kernel is in gemm_dmma.cu.)
 //
 // Packed operands are MN-major (element (kk, mm) at kk*ld + mm) and padded with zeros
@@ -29,7 +32,17 @@ namespace {
 template <typename T, int H> struct VecT;
 template <> struct VecT<float, 4> { using V = float4; };
 template <> struct VecT<float, 2> { using V = float2; };
+template <> struct VecT<float, 1> { using V = float; };
 template <> struct VecT<double, 2> { using V = double2; };
+template <> struct VecT<double, 1> { using V = double; };
+
+// Offset within the tile of a thread's i-th accumulator row (or column), t = the
+// thread's row (column) index in the 16 x 16 thread grid.
+template <int H>
+__device__ __forceinline__ int frag_off(int t, int i) {
+  if constexpr (H == 1) return 2 * t + i;
+  else return i < H ? t * H + i : 16 * H + t * H + (i - H);
+}
 
 template <typename T, int H>
 __device__ __forceinline__ void unpack(const typename VecT<T, H>::V& v, T* o) {
@@ -47,16 +60,18 @@ struct SimtSmem {
   __align__(16) T Bs[SIMT_STAGES][TK][TM];
 };
 
-// Asynchronous global -> shared copy of one vector of BYTES (16 or 8) bytes; both
+// Asynchronous global -> shared copy of one vector of BYTES (16, 8 or 4) bytes; both
 // addresses must be BYTES-aligned.
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  static_assert(BYTES == 16 || BYTES == 8, "vector copies only");
+  static_assert(BYTES == 16 || BYTES == 8 || BYTES == 4, "cp.async sizes");
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
   if constexpr (BYTES == 16)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-  else
+  else if constexpr (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -107,10 +122,15 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
       T a[R], b[R];
-      unpack<T, H>(*reinterpret_cast<const V*>(&sm.As[buf][kk][tm * H]), a);
-      unpack<T, H>(*reinterpret_cast<const V*>(&sm.As[buf][kk][TM / 2 + tm * H]), a + H);
-      unpack<T, H>(*reinterpret_cast<const V*>(&sm.Bs[buf][kk][tn * H]), b);
-      unpack<T, H>(*reinterpret_cast<const V*>(&sm.Bs[buf][kk][TM / 2 + tn * H]), b + H);
+      if constexpr (H == 1) {
+        unpack<T, 2>(*reinterpret_cast<const typename VecT<T, 2>::V*>(&sm.As[buf][kk][2 * tm]), a);
+        unpack<T, 2>(*reinterpret_cast<const typename VecT<T, 2>::V*>(&sm.Bs[buf][kk][2 * tn]), b);
+      } else {
+        unpack<T, H>(*reinterpret_cast<const V*>(&sm.As[buf][kk][tm * H]), a);
+        unpack<T, H>(*reinterpret_cast<const V*>(&sm.As[buf][kk][TM / 2 + tm * H]), a + H);
+        unpack<T, H>(*reinterpret_cast<const V*>(&sm.Bs[buf][kk][tn * H]), b);
+        unpack<T, H>(*reinterpret_cast<const V*>(&sm.Bs[buf][kk][TM / 2 + tn * H]), b + H);
+      }
 #pragma unroll
       for (int i = 0; i < R; ++i)
 #pragma unroll
@@ -122,22 +142,23 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
 
 template <typename T, int H, int CDT, int MODE>
 __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const T (&acc)[2 * H][2 * H]) {
-  constexpr int TM = 32 * H, R = 2 * H;
+  constexpr int R = 2 * H;
+  constexpr int EB = (H == 1) ? 2 : H;   // C elements loaded together
   const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
-  auto row_of = [&](int i) -> int64_t { return m0 + (i < H ? tm * H + i : TM / 2 + tm * H + (i - H)); };
-  auto col_of = [&](int j) -> int64_t { return n0 + (j < H ? tn * H + j : TM / 2 + tn * H + (j - H)); };
-  // H elements of one row (or row pair) of the thread's block at a time: their C loads
-  // first, then the updates
+  auto row_of = [&](int i) -> int64_t { return m0 + frag_off<H>(tm, i); };
+  auto col_of = [&](int j) -> int64_t { return n0 + frag_off<H>(tn, j); };
+  // EB elements of one row (or row pair) of the thread's block at a time: their C
+  // loads first, then the updates
   if constexpr (MODE == OUT_ROWPAIR) {
 #pragma unroll
     for (int i = 0; i < R; i += 2)
 #pragma unroll
-      for (int j0 = 0; j0 < R; j0 += H) {
-        COld<CDT> old[H];
+      for (int j0 = 0; j0 < R; j0 += EB) {
+        COld<CDT> old[EB];
 #pragma unroll
-        for (int j = 0; j < H; ++j) old[j] = epi_load<CDT>(e, row_of(i) >> 1, col_of(j0 + j));
+        for (int j = 0; j < EB; ++j) old[j] = epi_load<CDT>(e, row_of(i) >> 1, col_of(j0 + j));
 #pragma unroll
-        for (int j = 0; j < H; ++j)
+        for (int j = 0; j < EB; ++j)
           epi_update<T, CDT, MODE>(e, row_of(i) >> 1, col_of(j0 + j), acc[i][j0 + j], acc[i + 1][j0 + j], old[j]);
       }
   } else if constexpr (MODE == OUT_COLPAIR) {
@@ -154,12 +175,12 @@ __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int6
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j0 = 0; j0 < R; j0 += H) {
-        COld<CDT> old[H];
+      for (int j0 = 0; j0 < R; j0 += EB) {
+        COld<CDT> old[EB];
 #pragma unroll
-        for (int j = 0; j < H; ++j) old[j] = epi_load<CDT>(e, row_of(i), col_of(j0 + j));
+        for (int j = 0; j < EB; ++j) old[j] = epi_load<CDT>(e, row_of(i), col_of(j0 + j));
 #pragma unroll
-        for (int j = 0; j < H; ++j)
+        for (int j = 0; j < EB; ++j)
           epi_update<T, CDT, MODE>(e, row_of(i), col_of(j0 + j), acc[i][j0 + j], T(0), old[j]);
       }
   }
@@ -221,8 +242,8 @@ simt_gemm_partial(GemmArgs g, int64_t kslice, T* __restrict__ ws) {
   for (int i = 0; i < 2 * H; ++i)
 #pragma unroll
     for (int j = 0; j < 2 * H; ++j) {
-      const int64_t row = m0 + (i < H ? tm * H + i : TM / 2 + tm * H + (i - H));
-      const int64_t col = n0 + (j < H ? tn * H + j : TM / 2 + tn * H + (j - H));
+      const int64_t row = m0 + frag_off<H>(tm, i);
+      const int64_t col = n0 + frag_off<H>(tn, j);
       out[col * g.Mp + row] = acc[i][j];
     }
 }
@@ -281,6 +302,8 @@ int variant_tile(int variant) {
     case VAR_FFMA_64: return 64;
     case VAR_DFMA_64: return 64;
     case VAR_DMMA_64: return 64;
+    case VAR_DFMA_32: return 32;
+    case VAR_FFMA_32: return 32;
   }
   return 0;
 }
@@ -345,6 +368,8 @@ cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const Group
     case VAR_FFMA_128: simt_gemm_grouped<float, 4><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_FFMA_64: simt_gemm_grouped<float, 2><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_DFMA_64: simt_gemm_grouped<double, 2><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_DFMA_32: simt_gemm_grouped<double, 1><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
+    case VAR_FFMA_32: simt_gemm_grouped<float, 1><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_DMMA_64: return launch_dmma_grouped(probs, tiles, ntiles, counter, sched, grid, s);
     default: return cudaErrorInvalidValue;
   }
@@ -358,6 +383,8 @@ int grouped_blocks_per_sm(int variant) {
     case VAR_FFMA_128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 4>, 256, 0); break;
     case VAR_FFMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 2>, 256, 0); break;
     case VAR_DFMA_64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 2>, 256, 0); break;
+    case VAR_DFMA_32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 1>, 256, 0); break;
+    case VAR_FFMA_32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 1>, 256, 0); break;
     case VAR_DMMA_64: return dmma_grouped_blocks_per_sm();
   }
   if (e != cudaSuccess) {

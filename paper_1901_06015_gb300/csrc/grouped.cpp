@@ -255,13 +255,12 @@ int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int metho
   Bucket& bd = g->buckets[1];
   bs.comp_double = 0;
   bs.plan_method = MXG_METHOD_FFMA;
-  bs.candidates = (method_s == MXG_METHOD_AUTO) ? std::vector<int>{VAR_FFMA_128, VAR_FFMA_64}
-                                                 : std::vector<int>{VAR_FFMA_128, VAR_FFMA_64};
+  bs.candidates = {VAR_FFMA_128, VAR_FFMA_64, VAR_FFMA_32};
   bd.comp_double = 1;
   bd.plan_method = (method_d == MXG_METHOD_DFMA) ? MXG_METHOD_DFMA : MXG_METHOD_DMMA;
-  bd.candidates = (method_d == MXG_METHOD_AUTO)   ? std::vector<int>{VAR_DMMA_64, VAR_DFMA_64}
+  bd.candidates = (method_d == MXG_METHOD_AUTO)   ? std::vector<int>{VAR_DMMA_64, VAR_DFMA_64, VAR_DFMA_32}
                   : (method_d == MXG_METHOD_DMMA) ? std::vector<int>{VAR_DMMA_64}
-                                                  : std::vector<int>{VAR_DFMA_64};
+                                                  : std::vector<int>{VAR_DFMA_64, VAR_DFMA_32};
   g->plans.resize(static_cast<size_t>(count));
   for (int64_t i = 0; i < count; ++i) {
     const mxg_problem& q = probs[i];
@@ -447,7 +446,7 @@ int mxg_group_run(mxg_group g) {
 
 int mxg_group_describe(mxg_group g, char* buf, size_t len) {
   if (!g || !buf || len == 0) return MXG_EINVAL;
-  static const char* vnames[] = {"ffma_128", "ffma_64", "dfma_64", "dfma_32", "dmma_64"};
+  static const char* vnames[VAR_COUNT] = {"ffma_128", "ffma_64", "dfma_64", "dfma_32", "dmma_64", "ffma_32"};
   std::string s = "{\"problems\": " + std::to_string(g->plans.size()) + ", \"graph\": " +
                   (g->exec ? "true" : "false") + ", \"arena_bytes\": " + std::to_string(g->arena_bytes) +
                   ", \"scale_only\": " + std::to_string(g->scale_list.size()) + ", \"buckets\": [";
@@ -507,7 +506,7 @@ int mxg_tune_load(const char* path) {
   double ms = 0.0;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   while (std::fscanf(f, "%159s %d %d %lf", sig, &v, &s, &ms) == 4) {
-    if (v >= VAR_FFMA_128 && v <= VAR_DMMA_64 && v != VAR_DFMA_32 && (s == SCHED_DYNAMIC || s == SCHED_STATIC))
+    if (v >= 0 && v < VAR_COUNT && (s == SCHED_DYNAMIC || s == SCHED_STATIC))
       g_tune[sig] = TuneRec{v, s, ms};
   }
   std::fclose(f);

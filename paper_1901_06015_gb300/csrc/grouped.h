@@ -10,9 +10,11 @@ enum GroupVariant : int {
   VAR_FFMA_128 = 0,   // FP32 FFMA, 128 x 128
   VAR_FFMA_64 = 1,    // FP32 FFMA, 64 x 64
   VAR_DFMA_64 = 2,    // FP64 DFMA, 64 x 64
-  VAR_DFMA_32 = 3,    // reserved (not built: the complex epilogue needs row pairs per thread)
-  VAR_DMMA_64 = 4     // FP64 DMMA, 64 x 64
+  VAR_DFMA_32 = 3,    // FP64 DFMA, 32 x 32
+  VAR_DMMA_64 = 4,    // FP64 DMMA, 64 x 64
+  VAR_FFMA_32 = 5     // FP32 FFMA, 32 x 32
 };
+constexpr int VAR_COUNT = 6;
 
 // Tile schedules of the persistent kernels: DYNAMIC takes the next entry of the
 // (longest-first) work list from an atomic counter; STATIC gives CTA b the entries

@@ -138,3 +138,37 @@ def test_one_shot_grouped_call():
         ref = oracle_mxgemm("n", "n", p["alpha"], p["A"], p["B"], p["beta"], ref_C, comp=p["combo"][3])
         err, _ = normwise_error(p["combo"], dC.cpu().numpy(), ref, p["A"], p["B"], p["C"], p["alpha"], p["beta"])
         assert err <= tolerance(p["combo"], p["A"].shape[1])
+
+
+@pytest.mark.parametrize("method_d,variant,solo_d", [
+    ("dmma", 4, "dmma"),   # DMMA 64 x 64
+    ("dfma", 2, "dfma"),   # DFMA 64 x 64
+    ("dfma", 3, "dfma"),   # DFMA 32 x 32 (adjacent row pairs per thread)
+])
+@pytest.mark.parametrize("variant_s", [0, 1, 5])   # FFMA 128, 64, 32
+def test_every_grouped_kernel_equals_solo(tmp_path, method_d, variant, solo_d, variant_s):
+    """Each contraction kernel of the grouped launch, forced through a loaded tuning
+    file, gives every problem bit for bit the result of the same problem run alone with
+    the same method family (each element is accumulated by one thread in increasing k,
+    whatever the tile). Shapes, transposes and storage orders are mixed, so ragged
+    edges, complex row/column pairs and every output mode occur."""
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(11, 48, lo=1, hi=140)
+    items, _ = _device_items(probs)
+    probe = mx.Group(items, method_d=method_d, tune=False, graph=False)
+    sigs = {b["precision"]: b["signature"] for b in probe.describe()["buckets"]}
+    probe.close()
+    path = tmp_path / "tune.txt"
+    path.write_text("".join(f"{sigs[p]} {v} 0 1.0\n" for p, v in (("s", variant_s), ("d", variant)) if p in sigs))
+    assert mx.mxg_tune_load(str(path)) == 0
+    items, dev = _device_items(probs)
+    g = mx.Group(items, method_d=method_d, tune=False, graph=True)
+    kernels = {b["precision"]: b["kernel"] for b in g.describe()["buckets"]}
+    names = {0: "ffma_128", 1: "ffma_64", 5: "ffma_32", 2: "dfma_64", 3: "dfma_32", 4: "dmma_64"}
+    assert kernels.get("s", names[variant_s]) == names[variant_s]
+    assert kernels.get("d", names[variant]) == names[variant]
+    g.run()
+    torch.cuda.synchronize()
+    for p, (_, _, dC) in zip(probs, dev):
+        assert np.array_equal(dC.cpu().numpy(), _solo(p, method_d=solo_d)), (p["combo"], p["ta"], p["tb"])
+    g.close()
