@@ -627,13 +627,16 @@ def run_serving(args):
     gaps = rng.exponential(1.0 / lam, size=N)
     arrivals = np.cumsum(gaps)
 
-    def serve(fifo):
+    def serve(fifo, burst=0):
+        """Serve the trace (Poisson arrivals), or with burst > 0 its first `burst` requests
+        submitted at once (saturation: the completion rate is the form's capacity)."""
         srv = mx.Server(n_streams=1 if fifo else args.streams, hbm_budget_bytes=args.budget_gb << 30,
                         small_flops=args.small_flops, fifo=fifo)
-        arr = [mx.make_problems([item(r)])[0] for r in reqs]
+        todo = reqs[:burst] if burst else reqs
+        arr = [mx.make_problems([item(r)])[0] for r in todo]
         base = srv.now()
-        for i in range(N):
-            target = base + arrivals[i]
+        for i in range(len(todo)):
+            target = base + (0.0 if burst else arrivals[i])
             while True:
                 d = target - srv.now()
                 if d <= 0:
@@ -642,12 +645,13 @@ def run_serving(args):
             rid = __import__("ctypes").c_uint64(0)
             mx.lib().mxg_server_submit(srv.s, arr[i], __import__("ctypes").byref(rid))
         srv.drain(3600)
-        comps = srv.poll(N + 10)
+        comps = srv.poll(len(todo) + 10)
         st = srv.stats()
         srv.close()
         lat = np.array([c["done"] - c["arrival"] for c in comps if c["status"] == 0])
         t_first = min(c["arrival"] for c in comps); t_last = max(c["done"] for c in comps)
-        return {"requests_per_s": len(lat) / (t_last - t_first), "gflops": total_flops / (t_last - t_first) / 1e9,
+        fl = sum(r[6] for r in todo)
+        return {"requests_per_s": len(lat) / (t_last - t_first), "gflops": fl / (t_last - t_first) / 1e9,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p90_ms": float(np.percentile(lat, 90) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
                 "failed": int(st["failed"]), "max_in_flight": int(st["max_in_flight"]),
@@ -657,6 +661,15 @@ def run_serving(args):
     sampler.start()
     served = serve(False)
     serial = serve(True)
+    sat = None
+    if args.saturation > 0:
+        b = min(args.saturation, N)
+        sat_served, sat_serial = serve(False, b), serve(True, b)
+        sat = {"requests": b, "served_requests_per_s": sat_served["requests_per_s"],
+               "serial_requests_per_s": sat_serial["requests_per_s"],
+               "served_gflops": sat_served["gflops"], "serial_gflops": sat_serial["gflops"],
+               "capacity_ratio": sat_served["requests_per_s"] / sat_serial["requests_per_s"],
+               "served_failed": sat_served["failed"], "serial_failed": sat_serial["failed"]}
     clocks = sampler.stop()
     line = {"metric": METRIC, "workload": "serving", "value": served["requests_per_s"], "unit": "requests/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
@@ -669,7 +682,7 @@ def run_serving(args):
             "capacity_requests_per_s": capacity, "arrival_rate": lam, "mean_service_ms": mean_service * 1e3,
             "mean_request_gflop": total_flops / N / 1e9, "served": served, "serial": serial,
             "p99_speedup_vs_serial": serial["p99_ms"] / served["p99_ms"],
-            "p50_speedup_vs_serial": serial["p50_ms"] / served["p50_ms"], "clocks": clocks}
+            "p50_speedup_vs_serial": serial["p50_ms"] / served["p50_ms"], "saturation": sat, "clocks": clocks}
     print(json.dumps(line))
     return 0
 
@@ -754,6 +767,8 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=48)
     ap.add_argument("--small-flops", type=float, default=2e8)
     ap.add_argument("--capacity-sample", type=int, default=3000)
+    ap.add_argument("--saturation", type=int, default=5000,
+                    help="serving: also submit this many requests at once to each form (0: skip)")
     ap.add_argument("--sizes", default="4096,8192,16384")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
