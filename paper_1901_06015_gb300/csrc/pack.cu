@@ -68,16 +68,21 @@ __device__ __forceinline__ double mul_add(double a, double b, double c, double d
   return __dadd_rn(__dmul_rn(a, b), __dmul_rn(c, d));
 }
 
-template <typename DT>
-__device__ __forceinline__ DT pattern_value(int pattern, int s, int t, DT xr, DT xi) {
-  // (for a real source the planner only uses PAT_RE, so xi is never read there)
-  switch (pattern) {
-    case PAT_SPLIT_MN: return t ? xi : xr;
-    case PAT_SPLIT_K: return s ? xi : xr;
-    case PAT_ONE_E: return s == 0 ? (t ? xi : xr) : (t ? xr : -xi);
-    default: return xr;
-  }
+// Value of packed element (k-row sub-index s, mn-column sub-index t) of logical element
+// (xr, xi) under pattern PAT (a real source only ever uses PAT_RE, so xi is not read
+// there).
+template <int PAT, typename DT>
+__device__ __forceinline__ DT pattern_value(int s, int t, DT xr, DT xi) {
+  if constexpr (PAT == PAT_SPLIT_MN) return t ? xi : xr;
+  else if constexpr (PAT == PAT_SPLIT_K) return s ? xi : xr;
+  else if constexpr (PAT == PAT_ONE_E) return s == 0 ? (t ? xi : xr) : (t ? xr : -xi);
+  else return xr;
 }
+// Packed rows per logical k (FK) and packed columns per logical mn (FM) of a pattern.
+template <int PAT> struct PatDim {
+  static constexpr int FK = (PAT == PAT_SPLIT_K || PAT == PAT_ONE_E) ? 2 : 1;
+  static constexpr int FM = (PAT == PAT_SPLIT_MN || PAT == PAT_ONE_E) ? 2 : 1;
+};
 
 constexpr int PK_MN = 64, PK_P = 32;   // logical tile: 64 (mn) x 32 (p) elements
 
@@ -97,42 +102,54 @@ template <typename DT> struct OutVec<SPLIT_BF16_ONE, DT> { static constexpr int 
 
 // One 64 (mn) x 32 (p) tile of logical elements starting at (mn0, p0): read it with
 // the lanes along the source's unit-stride dimension (8 independent loads per
-// thread), keep it in shared memory, and write the 32*fk x 64*fm packed sub-block as
-// 16-byte vectors along the packed operand's contiguous dimension (MN for the SIMT
-// layout, K for the tensor-core planes). Padded extents are multiples of the vector
-// width, so a vector is either wholly inside or wholly outside them. Ends with the
-// block synchronised.
-template <int SDT, typename DT, int LAYOUT, int SPLIT>
+// thread, addressed from one base pointer and a fixed step; bounds checked only in
+// tiles that cross the logical extent), keep it in shared memory, and write the
+// 32*FK x 64*FM packed sub-block as 16-byte vectors along the packed operand's
+// contiguous dimension (MN for the SIMT layout, K for the tensor-core planes). The
+// pattern is a template parameter, so the index arithmetic of the write-out is
+// shifts and masks. Padded extents are multiples of the vector width, so a vector is
+// either wholly inside or wholly outside them. Ends with the block synchronised.
+template <int SDT, typename DT, int LAYOUT, int SPLIT, int PAT>
 __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_t p0, PackSmem<DT>& sm) {
   using ST = typename SrcT<SDT>::T;
   constexpr bool SC = SrcT<SDT>::cplx;
   constexpr int V = OutVec<SPLIT, DT>::n;
+  constexpr int FK = PatDim<PAT>::FK, FM = PatDim<PAT>::FM;
+  constexpr int64_t CM = SC ? 2 : 1;   // stored components per element
   const int t = threadIdx.x;
   const bool unit_mn = (a.smn == 1);
-  const int fk = (a.pattern == PAT_SPLIT_K || a.pattern == PAT_ONE_E) ? 2 : 1;
-  const int fm = (a.pattern == PAT_SPLIT_MN || a.pattern == PAT_ONE_E) ? 2 : 1;
-  ST vr_[8], vi_[8];
-  int lm_[8], lp_[8];
-  bool in_[8];
+  // element i of this thread: (lm0 + i*dm, lp0 + i*dp)
+  const int lm0 = unit_mn ? (t & 63) : (t >> 5), lp0 = unit_mn ? (t >> 6) : (t & 31);
+  const int dm = unit_mn ? 0 : 8, dp = unit_mn ? 4 : 0;
+  ST vr[8], vi[8];
+  const ST* src = static_cast<const ST*>(a.src);
+  if (mn0 + PK_MN <= a.MN && p0 + PK_P <= a.K) {
+    const ST* sp = src + ((mn0 + lm0) * a.smn + (p0 + lp0) * a.sk) * CM;
+    const int64_t step = (dm * a.smn + dp * a.sk) * CM;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int lm = unit_mn ? (t & 63) : ((t >> 5) + 8 * i);
-    const int lp = unit_mn ? ((t >> 6) + 4 * i) : (t & 31);
-    const int64_t mn = mn0 + lm, p = p0 + lp;
-    lm_[i] = lm; lp_[i] = lp;
-    in_[i] = (mn < a.MN && p < a.K);
-    vr_[i] = ST(0.0f); vi_[i] = ST(0.0f);
-    if (in_[i]) {
-      const ST* sp = static_cast<const ST*>(a.src) + (mn * a.smn + p * a.sk) * (SC ? 2 : 1);
-      vr_[i] = __ldg(sp);
-      if constexpr (SC) vi_[i] = __ldg(sp + 1);
+    for (int i = 0; i < 8; ++i) {
+      vr[i] = __ldg(sp + i * step);
+      if constexpr (SC) vi[i] = __ldg(sp + i * step + 1);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t mn = mn0 + lm0 + i * dm, p = p0 + lp0 + i * dp;
+      vr[i] = ST(0.0f);
+      vi[i] = ST(0.0f);
+      if (mn < a.MN && p < a.K) {
+        const ST* sp = src + (mn * a.smn + p * a.sk) * CM;
+        vr[i] = __ldg(sp);
+        if constexpr (SC) vi[i] = __ldg(sp + 1);
+      }
     }
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    DT re = widen<DT>(vr_[i]);
-    if constexpr (SC) {   // a real source only ever uses the RE pattern
-      DT im = widen<DT>(vi_[i]);
+    const int lm = lm0 + i * dm, lp = lp0 + i * dp;
+    DT re = widen<DT>(vr[i]);
+    if constexpr (SC) {
+      DT im = widen<DT>(vi[i]);
       if (a.conj) im = -im;
       if (a.fold) {       // alpha * x in the computation precision (literal complex alpha)
         const DT fr = static_cast<DT>(a.fold_re), fi = static_cast<DT>(a.fold_im);
@@ -140,36 +157,38 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
         re = nr;
         im = ni;
       }
-      sm.im[lp_[i]][lm_[i]] = im;
+      sm.im[lp][lm] = im;
     }
-    sm.re[lp_[i]][lm_[i]] = re;
+    sm.re[lp][lm] = re;
   }
   __syncthreads();
-  const int nk_out = PK_P * fk, nm_out = PK_MN * fm;
+  constexpr int NK = PK_P * FK, NM = PK_MN * FM;
+  auto value = [&](int r, int c) -> DT {   // packed element (row r of k, column c of mn) of the tile
+    const int lp = r / FK, sk = r % FK, lm = c / FM, tt = c % FM;
+    if constexpr (SC) return pattern_value<PAT, DT>(sk, tt, sm.re[lp][lm], sm.im[lp][lm]);
+    else return sm.re[lp][lm];
+  };
   if constexpr (LAYOUT == LAYOUT_MN_MAJOR) {
-    const int vec_per_row = nm_out / V, total = nk_out * vec_per_row;
-    for (int idx = t; idx < total; idx += 256) {
-      const int r = idx / vec_per_row, c0 = (idx - r * vec_per_row) * V;
-      const int64_t kk = p0 * fk + r, mm = mn0 * fm + c0;
+    constexpr int VPR = NM / V, TOTAL = NK * VPR;
+#pragma unroll 1
+    for (int idx = t; idx < TOTAL; idx += 256) {
+      const int r = idx / VPR, c0 = (idx % VPR) * V;
+      const int64_t kk = p0 * FK + r, mm = mn0 * FM + c0;
       if (kk >= a.Kp || mm >= a.MNp) continue;
-      const int lp = r / fk, s = r - lp * fk;
       DT v[V];
 #pragma unroll
-      for (int u = 0; u < V; ++u) {
-        const int c = c0 + u, lm = c / fm, tt = c - lm * fm;
-        v[u] = SC ? pattern_value<DT>(a.pattern, s, tt, sm.re[lp][lm], sm.im[lp][lm]) : sm.re[lp][lm];
-      }
+      for (int u = 0; u < V; ++u) v[u] = value(r, c0 + u);
       DT* dst = static_cast<DT*>(a.dst) + kk * a.ld + mm;
       if constexpr (V == 4) *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
       else *reinterpret_cast<double2*>(dst) = make_double2(v[0], v[1]);
     }
   } else {
-    const int vec_per_row = nk_out / V, total = nm_out * vec_per_row;
-    for (int idx = t; idx < total; idx += 256) {
-      const int c = idx / vec_per_row, r0 = (idx - c * vec_per_row) * V;
-      const int64_t kk = p0 * fk + r0, mm = mn0 * fm + c;
+    constexpr int VPR = NK / V, TOTAL = NM * VPR;
+#pragma unroll 1
+    for (int idx = t; idx < TOTAL; idx += 256) {
+      const int c = idx / VPR, r0 = (idx % VPR) * V;
+      const int64_t kk = p0 * FK + r0, mm = mn0 * FM + c;
       if (kk >= a.Kp || mm >= a.MNp) continue;
-      const int lm = c / fm, tt = c - lm * fm;
       const int64_t off = mm * a.ld + kk;
       if constexpr (SPLIT == SPLIT_F16_ONE || SPLIT == SPLIT_BF16_ONE) {
         // one plane rounded once from the working type (TC16)
@@ -177,8 +196,7 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
         uint16_t* p16 = reinterpret_cast<uint16_t*>(&pk);
 #pragma unroll
         for (int u = 0; u < V; ++u) {
-          const int r = r0 + u, lp = r / fk, s = r - lp * fk;
-          const DT x = SC ? pattern_value<DT>(a.pattern, s, tt, sm.re[lp][lm], sm.im[lp][lm]) : sm.re[lp][lm];
+          const DT x = value(r0 + u, c);
           if constexpr (SPLIT == SPLIT_F16_ONE) {
             const __half hv = to_f16(x);
             p16[u] = *reinterpret_cast<const uint16_t*>(&hv);
@@ -188,56 +206,72 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
           }
         }
         *reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.dst) + off) = pk;
-        continue;
       } else {
-      float hi[V], lo[V];
+        float hi[V], lo[V];
 #pragma unroll
-      for (int u = 0; u < V; ++u) {
-        const int r = r0 + u, lp = r / fk, s = r - lp * fk;
-        const float x = static_cast<float>(SC ? pattern_value<DT>(a.pattern, s, tt, sm.re[lp][lm], sm.im[lp][lm])
-                                              : sm.re[lp][lm]);
+        for (int u = 0; u < V; ++u) {
+          const float x = static_cast<float>(value(r0 + u, c));
+          if constexpr (SPLIT == SPLIT_TF32) {
+            hi[u] = tf32_rne(x);
+            lo[u] = tf32_rne(x - hi[u]);
+          } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            hi[u] = __bfloat162float(h);
+            lo[u] = x - hi[u];
+          }
+        }
         if constexpr (SPLIT == SPLIT_TF32) {
-          hi[u] = tf32_rne(x);
-          lo[u] = tf32_rne(x - hi[u]);
+          *reinterpret_cast<float4*>(static_cast<float*>(a.dst) + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<float4*>(static_cast<float*>(a.dst_lo) + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         } else {
-          const __nv_bfloat16 h = __float2bfloat16_rn(x);
-          hi[u] = __bfloat162float(h);
-          lo[u] = x - hi[u];
-        }
-      }
-      if constexpr (SPLIT == SPLIT_TF32) {
-        *reinterpret_cast<float4*>(static_cast<float*>(a.dst) + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<float4*>(static_cast<float*>(a.dst_lo) + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-      } else {
-        uint4 ph, pl;
-        uint32_t* h32 = reinterpret_cast<uint32_t*>(&ph);
-        uint32_t* l32 = reinterpret_cast<uint32_t*>(&pl);
+          uint4 ph, pl;
+          uint32_t* h32 = reinterpret_cast<uint32_t*>(&ph);
+          uint32_t* l32 = reinterpret_cast<uint32_t*>(&pl);
 #pragma unroll
-        for (int u = 0; u < V; u += 2) {
-          const __nv_bfloat162 hh = __floats2bfloat162_rn(hi[u], hi[u + 1]);   // exact: already bf16
-          const __nv_bfloat162 ll = __floats2bfloat162_rn(lo[u], lo[u + 1]);   // RN of x - hi
-          h32[u / 2] = *reinterpret_cast<const uint32_t*>(&hh);
-          l32[u / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+          for (int u = 0; u < V; u += 2) {
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(hi[u], hi[u + 1]);   // exact: already bf16
+            const __nv_bfloat162 ll = __floats2bfloat162_rn(lo[u], lo[u + 1]);   // RN of x - hi
+            h32[u / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+            l32[u / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+          }
+          *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst) + off) = ph;
+          *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst_lo) + off) = pl;
         }
-        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst) + off) = ph;
-        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.dst_lo) + off) = pl;
-      }
       }
     }
   }
   __syncthreads();
 }
 
-template <int SDT, typename DT, int LAYOUT, int SPLIT>
-__global__ void __launch_bounds__(256) pack_kernel(PackArgs a, int64_t ntile_p) {
+// Call f(IC<pattern>) for the pattern of a (a real source only ever has PAT_RE).
+template <int SDT, class F>
+__device__ __host__ __forceinline__ bool with_pattern(int pattern, F&& f) {
+  if constexpr (!SrcT<SDT>::cplx) {
+    if (pattern != PAT_RE) return false;
+    f(std::integral_constant<int, PAT_RE>{});
+    return true;
+  } else {
+    switch (pattern) {
+      case PAT_RE: f(std::integral_constant<int, PAT_RE>{}); return true;
+      case PAT_SPLIT_MN: f(std::integral_constant<int, PAT_SPLIT_MN>{}); return true;
+      case PAT_SPLIT_K: f(std::integral_constant<int, PAT_SPLIT_K>{}); return true;
+      case PAT_ONE_E: f(std::integral_constant<int, PAT_ONE_E>{}); return true;
+    }
+    return false;
+  }
+}
+
+template <int SDT, typename DT, int LAYOUT, int SPLIT, int PAT>
+__global__ void __launch_bounds__(256, 5) pack_kernel(PackArgs a, int64_t ntile_p) {
   __shared__ PackSmem<DT> sm;
   const int64_t mn0 = static_cast<int64_t>(blockIdx.x) * PK_MN;
-  for (int64_t tp = blockIdx.y; tp < ntile_p; tp += gridDim.y) pack_tile<SDT, DT, LAYOUT, SPLIT>(a, mn0, tp * PK_P, sm);
+  for (int64_t tp = blockIdx.y; tp < ntile_p; tp += gridDim.y)
+    pack_tile<SDT, DT, LAYOUT, SPLIT, PAT>(a, mn0, tp * PK_P, sm);
 }
 
 // Grouped pack: block b packs tile (b - tile_start[t]) of task t, where t is found by a
-// binary search of the tile prefix sums; the tasks' source datatypes differ, so the
-// source type is dispatched at run time (uniformly over the block).
+// binary search of the tile prefix sums; the tasks' source datatypes and patterns
+// differ, so both are dispatched at run time (uniformly over the block).
 template <typename DT>
 __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __restrict__ tasks,
                                                            const int64_t* __restrict__ tile_start, int ntasks) {
@@ -253,16 +287,30 @@ __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __res
   const int fm = pat_fm(a.pattern);
   const int64_t tiles_mn = (a.MNp / fm + PK_MN - 1) / PK_MN;
   const int64_t mn0 = (local % tiles_mn) * PK_MN, p0 = (local / tiles_mn) * PK_P;
+  auto run = [&](auto S) {
+    constexpr int SDT = decltype(S)::value;
+    with_pattern<SDT>(a.pattern, [&](auto P) {
+      pack_tile<SDT, DT, LAYOUT_MN_MAJOR, SPLIT_NONE, decltype(P)::value>(a, mn0, p0, sm);
+    });
+  };
   switch (a.src_dt) {
-    case MXG_S: pack_tile<MXG_S, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_D: pack_tile<MXG_D, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_C: pack_tile<MXG_C, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_Z: pack_tile<MXG_Z, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_H: pack_tile<MXG_H, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_K: pack_tile<MXG_K, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_B: pack_tile<MXG_B, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
-    case MXG_W: pack_tile<MXG_W, DT, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, mn0, p0, sm); break;
+    case MXG_S: run(std::integral_constant<int, MXG_S>{}); break;
+    case MXG_D: run(std::integral_constant<int, MXG_D>{}); break;
+    case MXG_C: run(std::integral_constant<int, MXG_C>{}); break;
+    case MXG_Z: run(std::integral_constant<int, MXG_Z>{}); break;
+    case MXG_H: run(std::integral_constant<int, MXG_H>{}); break;
+    case MXG_K: run(std::integral_constant<int, MXG_K>{}); break;
+    case MXG_B: run(std::integral_constant<int, MXG_B>{}); break;
+    case MXG_W: run(std::integral_constant<int, MXG_W>{}); break;
   }
+}
+
+template <int SDT, typename DT, int LAYOUT, int SPLIT>
+cudaError_t launch_pattern(const PackArgs& a, dim3 grid, int64_t ntp, cudaStream_t s) {
+  const bool ok = with_pattern<SDT>(a.pattern, [&](auto P) {
+    pack_kernel<SDT, DT, LAYOUT, SPLIT, decltype(P)::value><<<grid, 256, 0, s>>>(a, ntp);
+  });
+  return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
 template <int SDT>
@@ -273,22 +321,20 @@ cudaError_t launch_src(const PackArgs& a, int comp_double, cudaStream_t s) {
   if (ntm > 0x7fffffffLL) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(ntm), static_cast<unsigned>(ntp < 65535 ? ntp : 65535));
   if (a.split == SPLIT_NONE && a.layout == LAYOUT_MN_MAJOR) {
-    if (comp_double) pack_kernel<SDT, double, LAYOUT_MN_MAJOR, SPLIT_NONE><<<grid, 256, 0, s>>>(a, ntp);
-    else pack_kernel<SDT, float, LAYOUT_MN_MAJOR, SPLIT_NONE><<<grid, 256, 0, s>>>(a, ntp);
+    if (comp_double) return launch_pattern<SDT, double, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, grid, ntp, s);
+    return launch_pattern<SDT, float, LAYOUT_MN_MAJOR, SPLIT_NONE>(a, grid, ntp, s);
   } else if (a.split == SPLIT_TF32 && a.layout == LAYOUT_K_MAJOR && !comp_double) {
-    pack_kernel<SDT, float, LAYOUT_K_MAJOR, SPLIT_TF32><<<grid, 256, 0, s>>>(a, ntp);
+    return launch_pattern<SDT, float, LAYOUT_K_MAJOR, SPLIT_TF32>(a, grid, ntp, s);
   } else if (a.split == SPLIT_BF16 && a.layout == LAYOUT_K_MAJOR && !comp_double) {
-    pack_kernel<SDT, float, LAYOUT_K_MAJOR, SPLIT_BF16><<<grid, 256, 0, s>>>(a, ntp);
+    return launch_pattern<SDT, float, LAYOUT_K_MAJOR, SPLIT_BF16>(a, grid, ntp, s);
   } else if ((a.split == SPLIT_F16_ONE || a.split == SPLIT_BF16_ONE) && a.layout == LAYOUT_K_MAJOR) {
     // working type: the source's own precision, so the 16-bit rounding happens once
     constexpr bool src_double = (SDT == MXG_D || SDT == MXG_Z);
     using WT = typename std::conditional<src_double, double, float>::type;
-    if (a.split == SPLIT_F16_ONE) pack_kernel<SDT, WT, LAYOUT_K_MAJOR, SPLIT_F16_ONE><<<grid, 256, 0, s>>>(a, ntp);
-    else pack_kernel<SDT, WT, LAYOUT_K_MAJOR, SPLIT_BF16_ONE><<<grid, 256, 0, s>>>(a, ntp);
-  } else {
-    return cudaErrorInvalidValue;
+    if (a.split == SPLIT_F16_ONE) return launch_pattern<SDT, WT, LAYOUT_K_MAJOR, SPLIT_F16_ONE>(a, grid, ntp, s);
+    return launch_pattern<SDT, WT, LAYOUT_K_MAJOR, SPLIT_BF16_ONE>(a, grid, ntp, s);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
