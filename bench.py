@@ -732,12 +732,18 @@ def run_single(args):
             times.append(e0.elapsed_time(e1))
     pack_ms, con_ms, nl = h.phase_times()
     fl = 2.0 * mm * nn * kk * R
+    # C is read and written once in its storage type (beta = 1): with k = 0 the call is the
+    # stand-alone C := beta*C launch, with a small k the contraction kernel's time is
+    # dominated by its fused epilogue, so this is the epilogue's HBM rate
+    c_bytes = 2.0 * mm * nn * C.element_size() * (2 if C.dim() == 3 else 1)
+    c_ms = (con_ms / nl) if nl else min(times)
     line = {"workload": "single", "combo": combo, "method": args.method, "m_n_k": [mm, nn, kk], "reps": args.reps,
             "split_k": args.split_k,
             "layout": [la, lb, lc], "trans": [args.transa, args.transb],
             "best_ms": min(times), "gflops": fl / min(times) / 1e6,
             "contraction_ms_mean": con_ms / max(nl, 1), "pack_ms_mean": pack_ms / max(nl, 1),
-            "contraction_tflops": fl / (con_ms / max(nl, 1)) / 1e9 if nl else None}
+            "contraction_tflops": fl / (con_ms / max(nl, 1)) / 1e9 if nl else None,
+            "c_bytes": c_bytes, "c_gbs": c_bytes / c_ms / 1e6 if c_ms > 0 else None}
     print(json.dumps(line))
     return 0
 

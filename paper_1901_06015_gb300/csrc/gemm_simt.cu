@@ -267,17 +267,22 @@ __global__ void splitk_reduce(const T* __restrict__ ws, int splits, int64_t Mp, 
   }
 }
 
-// C := beta * C (k == 0 or alpha == 0: A and B are not read).
+// C := beta * C (k == 0 or alpha == 0: A and B are not read). Block (bx, by) walks
+// columns by, by + gridDim.y, ... and in each the rows 256*bx + t + 256*gridDim.x*u
+// (lanes along the rows, which are unit-stride after the whole-operation transpose),
+// four elements per thread at a time with their loads in flight together.
 template <int CDT>
-__global__ void scale_c_kernel(EpiArgs e) {
-  const int64_t total = e.m * e.n;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = idx % e.m, j = idx / e.m;
-    if constexpr (CStore<CDT>::cplx) {
-      epi_store<double, CDT, OUT_ROWPAIR>(e, i, j, 0.0, 0.0);
-    } else {
-      epi_store<double, CDT, OUT_REAL>(e, i, j, 0.0, 0.0);
+__global__ void __launch_bounds__(256) scale_c_kernel(EpiArgs e) {
+  constexpr int MODE = CStore<CDT>::cplx ? OUT_ROWPAIR : OUT_REAL;
+  constexpr int U = 4;
+  const int64_t rstep = static_cast<int64_t>(gridDim.x) * 256;
+  for (int64_t j = blockIdx.y; j < e.n; j += gridDim.y) {
+    for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; i0 < e.m; i0 += U * rstep) {
+      COld<CDT> old[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) old[u] = epi_load<CDT>(e, i0 + u * rstep, j);
+#pragma unroll
+      for (int u = 0; u < U; ++u) epi_update<double, CDT, MODE>(e, i0 + u * rstep, j, 0.0, 0.0, old[u]);
     }
   }
 }
@@ -395,13 +400,15 @@ int grouped_blocks_per_sm(int variant) {
 }
 
 cudaError_t launch_scale_c(const EpiArgs& e, int c_dt, cudaStream_t s) {
-  const int64_t total = e.m * e.n;
-  if (total <= 0) return cudaSuccess;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (e.m <= 0 || e.n <= 0) return cudaSuccess;
+  // about 16 blocks of 256 threads per SM in total: rows split into at most 8 row
+  // blocks of 4 x 256 rows per pass, columns over the rest
+  const int64_t gx = std::min<int64_t>((e.m + 1023) / 1024, 8);
+  const int64_t gy = std::min<int64_t>(e.n, std::max<int64_t>(1, (152 * 16) / gx));
+  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   const int mode = (c_dt == MXG_C || c_dt == MXG_Z || c_dt == MXG_K || c_dt == MXG_W) ? OUT_ROWPAIR : OUT_REAL;
   const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto) {
-    scale_c_kernel<decltype(C)::value><<<static_cast<unsigned>(blocks), 256, 0, s>>>(e);
+    scale_c_kernel<decltype(C)::value><<<grid, 256, 0, s>>>(e);
   });
   return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
