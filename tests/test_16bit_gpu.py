@@ -13,10 +13,10 @@ from tests.gpu_util import run, methods_for, to_device, from_device
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SAMPLE = [c for i, c in enumerate(synth.all_combos_16()) if i % 7 == 0]
+ALL_16 = synth.all_combos_16()   # the 1920 combinations with a 16-bit storage or precision
 
 
-@pytest.mark.parametrize("combo", SAMPLE)
+@pytest.mark.parametrize("combo", ALL_16)
 def test_16bit_parity(combo):
     m, n, k = 67, 45, 130
     A, B, C0 = synth.problem(23, combo, m, n, k, order_c="FC"[len(combo) % 2])
@@ -31,7 +31,7 @@ def test_16bit_parity(combo):
         assert err <= tolerance(combo, k, meth), (combo, meth, err, tolerance(combo, k, meth))
 
 
-@pytest.mark.parametrize("combo", [c for i, c in enumerate(synth.all_combos_16()) if i % 13 == 0])
+@pytest.mark.parametrize("combo", ALL_16)
 def test_16bit_small_integers_bit_exact(combo):
     """Integers in [-2, 2], k <= 16: every value is exact in binary16 and bfloat16, so
     the GPU result equals the oracle's rounded result bit for bit."""
