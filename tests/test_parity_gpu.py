@@ -65,9 +65,10 @@ def _case_reps():
 REPS = _case_reps()
 
 
-@pytest.mark.parametrize("combo", REPS)
+@pytest.mark.parametrize("combo", ALL)
 def test_trans_and_layouts(combo):
-    """All 16 trans pairs, column/row/general storage of every operand, ragged sizes."""
+    """All 16 trans pairs, column/row/general storage of every operand, ragged sizes,
+    for all 128 combinations and every method of the precision."""
     rng = np.random.default_rng(3)
     for ta, tb in itertools.product("ntch", repeat=2):
         m, n, k = (int(v) for v in rng.integers(1, 90, size=3))
@@ -89,7 +90,7 @@ def test_trans_and_layouts(combo):
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 9, 3), (17, 1, 5), (5, 6, 1), (129, 130, 131), (255, 33, 7)])
 def test_ragged_shapes(shape):
     m, n, k = shape
-    for combo in REPS:
+    for combo in ALL:
         A, B, C0 = synth.problem(4, combo, m, n, k)
         alpha = (1.0 + 0.5j) if all(c in "cz" for c in combo[:3]) else 1.5
         for meth in methods_for(combo):
