@@ -53,11 +53,18 @@ __device__ __forceinline__ void unpack(const typename VecT<T, H>::V& v, T* o) {
 
 constexpr int SIMT_STAGES = 4;
 
-template <typename T, int H>
+// Shared-memory ring of S k-tiles of TK rows of A' and B' (TM = 32H columns each).
+template <typename T, int H, int TK = 8, int S = SIMT_STAGES>
 struct SimtSmem {
-  static constexpr int TM = 32 * H, TK = 8;
-  __align__(16) T As[SIMT_STAGES][TK][TM];
-  __align__(16) T Bs[SIMT_STAGES][TK][TM];
+  static constexpr int TM = 32 * H;
+  __align__(16) T As[S][TK][TM];
+  __align__(16) T Bs[S][TK][TM];
+};
+// The single-problem 128 x 128 FFMA kernel takes k-tiles of 16 rows in a 3-stage ring
+// (48 KB): half the barriers of 8-row k-tiles. Every other kernel: 8 rows, 4 stages.
+template <typename T, int H> struct PlainTile {
+  static constexpr bool big = (sizeof(T) == 4 && H == 4);
+  static constexpr int TK = big ? 16 : 8, S = big ? 3 : SIMT_STAGES;
 };
 
 // Asynchronous global -> shared copy of one vector of BYTES (16, 8 or 4) bytes; both
@@ -78,17 +85,19 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Main loop of one 32H x 32H tile at (m0, n0); leaves the accumulators in acc. The
-// packed k-tiles stream global -> shared with cp.async through a SIMT_STAGES-deep ring
-// (each thread copies one vector -- H elements, 16 or 8 bytes -- of A' and one of B'
+// packed k-tiles stream global -> shared with cp.async through an S-deep ring (each
+// thread copies TK/8 vectors -- H elements, 16, 8 or 4 bytes -- of A' and as many of B'
 // per k-tile; each row of a k-tile is TM elements = 32 threads' vectors), so the loads
-// for k-tile kt + 3 are in flight while k-tile kt is computed.
-template <typename T, int H>
+// for k-tile kt + S - 1 are in flight while k-tile kt is computed.
+template <typename T, int H, int TK, int S>
 __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* __restrict__ B, int64_t lda,
                                               int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
-                                              SimtSmem<T, H>& sm, T (&acc)[2 * H][2 * H]) {
+                                              SimtSmem<T, H, TK, S>& sm, T (&acc)[2 * H][2 * H]) {
   using V = typename VecT<T, H>::V;
-  constexpr int TM = 32 * H, TK = 8, R = 2 * H, S = SIMT_STAGES;
-  constexpr int VB = static_cast<int>(sizeof(V));   // bytes each thread copies per operand and k-tile
+  constexpr int TM = 32 * H, R = 2 * H;
+  constexpr int CP = TK / 8;                          // rows each thread copies per operand and k-tile
+  static_assert(TK % 8 == 0, "k-tile rows: 8 per 256 threads");
+  constexpr int VB = static_cast<int>(sizeof(V));   // bytes per copied vector
   const int tid = threadIdx.x;
   const int lrow = tid / (TM / H), lcol = (tid % (TM / H)) * H;
   const T* Ag = A + lrow * lda + m0 + lcol;
@@ -98,8 +107,11 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
 #pragma unroll
   for (int st = 0; st < S - 1; ++st) {
     if (st < nk) {
-      cp_async<VB>(&sm.As[st][lrow][lcol], Ag + st * TK * lda);
-      cp_async<VB>(&sm.Bs[st][lrow][lcol], Bg + st * TK * ldb);
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        cp_async<VB>(&sm.As[st][lrow + 8 * c][lcol], Ag + (st * TK + 8 * c) * lda);
+        cp_async<VB>(&sm.Bs[st][lrow + 8 * c][lcol], Bg + (st * TK + 8 * c) * ldb);
+      }
     }
     cp_async_commit();
   }
@@ -114,8 +126,11 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
     const int64_t nxt = kt + S - 1;
     if (nxt < nk) {
       const int st = static_cast<int>(nxt % S);
-      cp_async<VB>(&sm.As[st][lrow][lcol], Ag + nxt * TK * lda);
-      cp_async<VB>(&sm.Bs[st][lrow][lcol], Bg + nxt * TK * ldb);
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        cp_async<VB>(&sm.As[st][lrow + 8 * c][lcol], Ag + (nxt * TK + 8 * c) * lda);
+        cp_async<VB>(&sm.Bs[st][lrow + 8 * c][lcol], Bg + (nxt * TK + 8 * c) * ldb);
+      }
     }
     cp_async_commit();
     const int buf = static_cast<int>(kt % S);
@@ -197,7 +212,7 @@ __device__ __forceinline__ void simt_epilogue_rt(int cdt, int mode, const EpiArg
 
 template <typename T, int H, int CDT, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmArgs g) {
-  __shared__ SimtSmem<T, H> sm;
+  __shared__ SimtSmem<T, H, PlainTile<T, H>::TK, PlainTile<T, H>::S> sm;
   T acc[2 * H][2 * H];
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 32 * H, n0 = static_cast<int64_t>(blockIdx.y) * 32 * H;
   simt_mainloop<T, H>(static_cast<const T*>(g.A), static_cast<const T*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, sm, acc);
@@ -291,7 +306,7 @@ __global__ void __launch_bounds__(256) scale_c_kernel(EpiArgs e) {
 
 TileCfg tile_cfg(int method) {
   switch (method) {
-    case MXG_METHOD_FFMA: return {128, 128, 8};
+    case MXG_METHOD_FFMA: return {128, 128, 16};
     case MXG_METHOD_DFMA: return {64, 64, 8};
     case MXG_METHOD_DMMA: return {64, 64, 16};
     case MXG_METHOD_TF32X3: return {128, 256, 16};   // tcgen05 tile 128 x 256, 64-byte k rows
