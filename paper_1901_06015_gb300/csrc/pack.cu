@@ -101,7 +101,7 @@ template <typename DT> struct OutVec<SPLIT_F16_ONE, DT> { static constexpr int n
 template <typename DT> struct OutVec<SPLIT_BF16_ONE, DT> { static constexpr int n = 8; };
 
 // One 64 (mn) x 32 (p) tile of logical elements starting at (mn0, p0): read it with
-// the lanes along the source's unit-stride dimension (8 independent loads per
+// the lanes along the source's smaller-stride dimension (8 independent loads per
 // thread, addressed from one base pointer and a fixed step; bounds checked only in
 // tiles that cross the logical extent), keep it in shared memory, and write the
 // 32*FK x 64*FM packed sub-block as 16-byte vectors along the packed operand's
@@ -117,7 +117,9 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
   constexpr int FK = PatDim<PAT>::FK, FM = PatDim<PAT>::FM;
   constexpr int64_t CM = SC ? 2 : 1;   // stored components per element
   const int t = threadIdx.x;
-  const bool unit_mn = (a.smn == 1);
+  // lanes along the dimension with the smaller stride (the unit-stride one for column-
+  // or row-stored operands; for general storage the closer-packed one)
+  const bool unit_mn = (a.smn <= a.sk);
   // element i of this thread: (lm0 + i*dm, lp0 + i*dp)
   const int lm0 = unit_mn ? (t & 63) : (t >> 5), lp0 = unit_mn ? (t >> 6) : (t & 31);
   const int dm = unit_mn ? 0 : 8, dp = unit_mn ? 4 : 0;

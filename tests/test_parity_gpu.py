@@ -65,10 +65,20 @@ def _case_reps():
 REPS = _case_reps()
 
 
+def _general(X):
+    """A view of X with no unit stride: every other row and every third column of a
+    larger zero-filled buffer."""
+    big = np.zeros((2 * X.shape[0] + 1, 3 * X.shape[1] + 2), dtype=X.dtype)
+    view = big[1::2, 2::3][:X.shape[0], :X.shape[1]]
+    view[...] = X
+    return view
+
+
 @pytest.mark.parametrize("combo", ALL)
 def test_trans_and_layouts(combo):
-    """All 16 trans pairs, column/row/general storage of every operand, ragged sizes,
-    for all 128 combinations and every method of the precision."""
+    """All 16 trans pairs, column/row/general storage of every operand (general: no
+    unit stride), ragged sizes, for all 128 combinations and every method of the
+    precision."""
     rng = np.random.default_rng(3)
     for ta, tb in itertools.product("ntch", repeat=2):
         m, n, k = (int(v) for v in rng.integers(1, 90, size=3))
@@ -80,6 +90,8 @@ def test_trans_and_layouts(combo):
             view = big[1::2, ::3][:m, :n]
             view[...] = C0
             C0 = view
+        A = _general(A) if rng.integers(3) == 0 else A   # general storage for A and B
+        B = _general(B) if rng.integers(3) == 0 else B
         alpha = (0.75 - 0.25j) if combo[:3] in ("zzz", "ccc", "zcz", "czc", "zzc", "ccz", "czz", "zcc") or \
             all(c in "cz" for c in combo[:3]) else 1.25
         beta = (0.5 + 0.5j) if combo[0] in "cz" else -0.75
