@@ -90,52 +90,67 @@ __device__ __forceinline__ COld<CDT> epi_load(const EpiArgs& e, int64_t i, int64
   return o;
 }
 
+// alpha in the computation precision and beta in C's storage precision, converted
+// from the double-precision arguments once per tile: a conversion from double runs on
+// the FP64 pipe, which on this chip is slow enough to stall an epilogue that converted
+// per element.
+template <typename AccT, int CDT>
+struct EpiScalars {
+  using CT = typename CStore<CDT>::T;
+  AccT ar, ai;
+  CT br, bi;
+  bool ai_zero;
+};
+
+template <typename AccT, int CDT>
+__device__ __forceinline__ EpiScalars<AccT, CDT> epi_scalars(const EpiArgs& e) {
+  using CT = typename CStore<CDT>::T;
+  return {static_cast<AccT>(e.ar), static_cast<AccT>(e.ai), to_ct<CT>(e.br), to_ct<CT>(e.bi), e.ai == 0.0};
+}
+
 // Update C(i, j) with the product value (pr, pi), both in the computation precision
-// AccT, given C's old value from epi_load. pi is ignored unless MODE pairs two real
-// results into one complex value. Order of operations (Sec. 7.1): t = alpha*P rounded
-// in AccT, cast to C's precision; beta*C formed in C's precision; their sum rounded in
-// C's precision.
+// AccT, given C's old value from epi_load and the converted scalars. pi is ignored
+// unless MODE pairs two real results into one complex value. Order of operations
+// (Sec. 7.1): t = alpha*P rounded in AccT, cast to C's precision; beta*C formed in C's
+// precision; their sum rounded in C's precision.
 template <typename AccT, int CDT, int MODE>
-__device__ __forceinline__ void epi_update(const EpiArgs& e, int64_t i, int64_t j, AccT pr, AccT pi,
-                                           const COld<CDT>& old) {
+__device__ __forceinline__ void epi_update(const EpiArgs& e, const EpiScalars<AccT, CDT>& sc, int64_t i, int64_t j,
+                                           AccT pr, AccT pi, const COld<CDT>& old) {
   using CT = typename CStore<CDT>::T;
   if (i >= e.m || j >= e.n) return;
-  const AccT ar = static_cast<AccT>(e.ar);
   CT* c = static_cast<CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
   if constexpr (!CStore<CDT>::cplx) {
     // C real: alpha and beta projected onto the real line (Sec. 7.2).
-    const CT t = to_ct<CT>(mul_rn(ar, pr));
-    c[0] = e.beta_zero ? t : add_rn(mul_rn(to_ct<CT>(e.br), old.re), t);
+    const CT t = to_ct<CT>(mul_rn(sc.ar, pr));
+    c[0] = e.beta_zero ? t : add_rn(mul_rn(sc.br, old.re), t);
   } else {
     AccT tr, ti;
-    const AccT ai_ = static_cast<AccT>(e.ai);
     if constexpr (MODE == OUT_RE_ONLY) {
-      tr = mul_rn(ar, pr);     // case 1c: the product is real; with a real alpha it reaches Re(C) only
-      ti = mul_rn(ai_, pr);    // (a complex alpha only under the literal reading)
+      tr = mul_rn(sc.ar, pr);     // case 1c: the product is real; with a real alpha it reaches Re(C) only
+      ti = mul_rn(sc.ai, pr);     // (a complex alpha only under the literal reading)
     } else {
-      const AccT ai = static_cast<AccT>(e.ai);
-      tr = sub_rn(mul_rn(ar, pr), mul_rn(ai, pi));  // complex alpha honoured (case 3)
-      ti = add_rn(mul_rn(ar, pi), mul_rn(ai, pr));  // ai == 0 otherwise
+      tr = sub_rn(mul_rn(sc.ar, pr), mul_rn(sc.ai, pi));  // complex alpha honoured (case 3)
+      ti = add_rn(mul_rn(sc.ar, pi), mul_rn(sc.ai, pr));  // ai == 0 otherwise
     }
     const CT tcr = to_ct<CT>(tr), tci = to_ct<CT>(ti);
     if (e.beta_zero) {
       c[0] = tcr;
-      c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? to_ct<CT>(0.0f) : tci;
+      c[1] = (MODE == OUT_RE_ONLY && sc.ai_zero) ? to_ct<CT>(0.0f) : tci;
     } else {
-      const CT br = to_ct<CT>(e.br), bi = to_ct<CT>(e.bi);
       const CT cr = old.re, ci = old.im;
-      const CT bcr = sub_rn(mul_rn(br, cr), mul_rn(bi, ci));
-      const CT bci = add_rn(mul_rn(br, ci), mul_rn(bi, cr));
+      const CT bcr = sub_rn(mul_rn(sc.br, cr), mul_rn(sc.bi, ci));
+      const CT bci = add_rn(mul_rn(sc.br, ci), mul_rn(sc.bi, cr));
       c[0] = add_rn(bcr, tcr);
-      c[1] = (MODE == OUT_RE_ONLY && e.ai == 0.0) ? bci : add_rn(bci, tci);
+      c[1] = (MODE == OUT_RE_ONLY && sc.ai_zero) ? bci : add_rn(bci, tci);
     }
   }
 }
 
 // Load, update and store one element of C.
 template <typename AccT, int CDT, int MODE>
-__device__ __forceinline__ void epi_store(const EpiArgs& e, int64_t i, int64_t j, AccT pr, AccT pi) {
-  epi_update<AccT, CDT, MODE>(e, i, j, pr, pi, epi_load<CDT>(e, i, j));
+__device__ __forceinline__ void epi_store(const EpiArgs& e, const EpiScalars<AccT, CDT>& sc, int64_t i, int64_t j,
+                                          AccT pr, AccT pi) {
+  epi_update<AccT, CDT, MODE>(e, sc, i, j, pr, pi, epi_load<CDT>(e, i, j));
 }
 
 }  // namespace mxg

@@ -101,6 +101,7 @@ __device__ __forceinline__ void dmma_epilogue(const EpiArgs& e, int64_t m0, int6
   constexpr int NOUT = (MODE == OUT_ROWPAIR || MODE == OUT_COLPAIR) ? DM_T * DM_T / 2 : DM_T * DM_T;
   constexpr int B = 8;
   static_assert(NOUT % (128 * B) == 0, "whole batches per thread");
+  const EpiScalars<double, CDT> sc = epi_scalars<double, CDT>(e);
   auto where = [&](int idx, int64_t* i, int64_t* j, int* o_r, int* o_i) {
     if constexpr (MODE == OUT_ROWPAIR) {
       const int rp = idx % (DM_T / 2), col = idx / (DM_T / 2);
@@ -127,7 +128,7 @@ __device__ __forceinline__ void dmma_epilogue(const EpiArgs& e, int64_t m0, int6
       int64_t i, j;
       int o_r, o_i;
       where(base + 128 * u, &i, &j, &o_r, &o_i);
-      epi_update<double, CDT, MODE>(e, i, j, Cs[o_r], o_i >= 0 ? Cs[o_i] : 0.0, old[u]);
+      epi_update<double, CDT, MODE>(e, sc, i, j, Cs[o_r], o_i >= 0 ? Cs[o_i] : 0.0, old[u]);
     }
   }
 }

@@ -159,6 +159,7 @@ template <typename T, int H, int CDT, int MODE>
 __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const T (&acc)[2 * H][2 * H]) {
   constexpr int R = 2 * H;
   constexpr int EB = (H == 1) ? 2 : H;   // C elements loaded together
+  const EpiScalars<T, CDT> sc = epi_scalars<T, CDT>(e);
   const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
   auto row_of = [&](int i) -> int64_t { return m0 + frag_off<H>(tm, i); };
   auto col_of = [&](int j) -> int64_t { return n0 + frag_off<H>(tn, j); };
@@ -174,7 +175,7 @@ __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int6
         for (int j = 0; j < EB; ++j) old[j] = epi_load<CDT>(e, row_of(i) >> 1, col_of(j0 + j));
 #pragma unroll
         for (int j = 0; j < EB; ++j)
-          epi_update<T, CDT, MODE>(e, row_of(i) >> 1, col_of(j0 + j), acc[i][j0 + j], acc[i + 1][j0 + j], old[j]);
+          epi_update<T, CDT, MODE>(e, sc, row_of(i) >> 1, col_of(j0 + j), acc[i][j0 + j], acc[i + 1][j0 + j], old[j]);
       }
   } else if constexpr (MODE == OUT_COLPAIR) {
 #pragma unroll
@@ -184,7 +185,7 @@ __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int6
       for (int j = 0; j < R; j += 2) old[j / 2] = epi_load<CDT>(e, row_of(i), col_of(j) >> 1);
 #pragma unroll
       for (int j = 0; j < R; j += 2)
-        epi_update<T, CDT, MODE>(e, row_of(i), col_of(j) >> 1, acc[i][j], acc[i][j + 1], old[j / 2]);
+        epi_update<T, CDT, MODE>(e, sc, row_of(i), col_of(j) >> 1, acc[i][j], acc[i][j + 1], old[j / 2]);
     }
   } else {
 #pragma unroll
@@ -196,7 +197,7 @@ __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int6
         for (int j = 0; j < EB; ++j) old[j] = epi_load<CDT>(e, row_of(i), col_of(j0 + j));
 #pragma unroll
         for (int j = 0; j < EB; ++j)
-          epi_update<T, CDT, MODE>(e, row_of(i), col_of(j0 + j), acc[i][j0 + j], T(0), old[j]);
+          epi_update<T, CDT, MODE>(e, sc, row_of(i), col_of(j0 + j), acc[i][j0 + j], T(0), old[j]);
       }
   }
 }
@@ -266,6 +267,7 @@ simt_gemm_partial(GemmArgs g, int64_t kslice, T* __restrict__ ws) {
 template <typename T, int CDT, int MODE>
 __global__ void splitk_reduce(const T* __restrict__ ws, int splits, int64_t Mp, int64_t Np, EpiArgs e) {
   const int64_t total = e.m * e.n, slice = Mp * Np;
+  const EpiScalars<T, CDT> sc = epi_scalars<T, CDT>(e);
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = idx % e.m, j = idx / e.m;
@@ -278,7 +280,7 @@ __global__ void splitk_reduce(const T* __restrict__ ws, int splits, int64_t Mp, 
       pr = add_rn(pr, ws[z * slice + o_r]);
       if (o_i >= 0) pi = add_rn(pi, ws[z * slice + o_i]);
     }
-    epi_store<T, CDT, MODE>(e, i, j, pr, pi);
+    epi_store<T, CDT, MODE>(e, sc, i, j, pr, pi);
   }
 }
 
@@ -291,13 +293,14 @@ __global__ void __launch_bounds__(256) scale_c_kernel(EpiArgs e) {
   constexpr int MODE = CStore<CDT>::cplx ? OUT_ROWPAIR : OUT_REAL;
   constexpr int U = 4;
   const int64_t rstep = static_cast<int64_t>(gridDim.x) * 256;
+  const EpiScalars<double, CDT> sc = epi_scalars<double, CDT>(e);
   for (int64_t j = blockIdx.y; j < e.n; j += gridDim.y) {
     for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; i0 < e.m; i0 += U * rstep) {
       COld<CDT> old[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) old[u] = epi_load<CDT>(e, i0 + u * rstep, j);
 #pragma unroll
-      for (int u = 0; u < U; ++u) epi_update<double, CDT, MODE>(e, i0 + u * rstep, j, 0.0, 0.0, old[u]);
+      for (int u = 0; u < U; ++u) epi_update<double, CDT, MODE>(e, sc, i0 + u * rstep, j, 0.0, 0.0, old[u]);
     }
   }
 }

@@ -200,8 +200,9 @@ __device__ __forceinline__ void tc_epi_load(const EpiArgs& e, int64_t row, int64
 }
 
 template <int CDT, int MODE>
-__device__ __forceinline__ void tc_epi_finish(const EpiArgs& e, int64_t row, int64_t col0, const uint32_t (&v)[32],
-                                              int lane, const COld<CDT> (&old)[TcChunk<MODE>::nold]) {
+__device__ __forceinline__ void tc_epi_finish(const EpiArgs& e, const EpiScalars<float, CDT>& sc, int64_t row,
+                                              int64_t col0, const uint32_t (&v)[32], int lane,
+                                              const COld<CDT> (&old)[TcChunk<MODE>::nold]) {
   if constexpr (MODE == OUT_ROWPAIR) {
     // per column pair (2t, 2t+1) one exchange: the even lane sends its value of column
     // 2t+1 and receives the odd lane's value of column 2t, so both lanes of the pair
@@ -212,17 +213,17 @@ __device__ __forceinline__ void tc_epi_finish(const EpiArgs& e, int64_t row, int
       const float ve = __uint_as_float(v[2 * t]), vo = __uint_as_float(v[2 * t + 1]);
       const float got = __shfl_xor_sync(0xffffffffu, odd ? ve : vo, 1);
       const float pr = odd ? got : ve, pi = odd ? vo : got;
-      epi_update<float, CDT, MODE>(e, row >> 1, col0 + 2 * t + (odd ? 1 : 0), pr, pi, old[t]);
+      epi_update<float, CDT, MODE>(e, sc, row >> 1, col0 + 2 * t + (odd ? 1 : 0), pr, pi, old[t]);
     }
   } else if constexpr (MODE == OUT_COLPAIR) {
 #pragma unroll
     for (int t = 0; t < 16; ++t)
-      epi_update<float, CDT, MODE>(e, row, (col0 >> 1) + t, __uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]),
+      epi_update<float, CDT, MODE>(e, sc, row, (col0 >> 1) + t, __uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]),
                                    old[t]);
   } else {
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj)
-      epi_update<float, CDT, MODE>(e, row, col0 + jj, __uint_as_float(v[jj]), 0.0f, old[jj]);
+      epi_update<float, CDT, MODE>(e, sc, row, col0 + jj, __uint_as_float(v[jj]), 0.0f, old[jj]);
   }
 }
 
@@ -366,13 +367,14 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b * TC_BN);
       with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
         constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
+        const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(g.e);
 #pragma unroll 1
         for (int c0 = 0; c0 < TC_BN; c0 += 32) {
           COld<CDT> old[TcChunk<MODE>::nold];
           tc_epi_load<CDT, MODE>(g.e, row, n0 + c0, lane, old);
           uint32_t v[32];
           tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-          tc_epi_finish<CDT, MODE>(g.e, row, n0 + c0, v, lane, old);
+          tc_epi_finish<CDT, MODE>(g.e, sc, row, n0 + c0, v, lane, old);
         }
       });
       // release the accumulator to the MMA warp
