@@ -308,6 +308,11 @@ int mxg_server_poll(mxg_server s, mxg_completion* out, int max, int* n);
 /* Block until every submitted request has completed (or timeout_s passes: MXG_ETIMEOUT). */
 int mxg_server_drain(mxg_server s, double timeout_s);
 int mxg_server_get_stats(mxg_server s, mxg_server_stats* st);
+/* Device error word of s (shared by its streams): nonzero if a device-side wait in a
+ * served request ran out of its limit since the last call to this function (which
+ * clears it). Waits for the work in flight on s's streams. Returns MXG_OK or
+ * MXG_ECUDA; *flag receives the word. */
+int mxg_server_check_device_error(mxg_server s, int* flag);
 double mxg_server_now(mxg_server s);
 /* Drains, stops the worker, frees the arena and streams. */
 int mxg_server_destroy(mxg_server s);

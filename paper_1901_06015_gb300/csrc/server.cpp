@@ -393,6 +393,28 @@ int mxg_server_get_stats(mxg_server s, mxg_server_stats* st) {
   return MXG_OK;
 }
 
+int mxg_server_check_device_error(mxg_server s, int* flag) {
+  if (!s || !flag) return MXG_EINVAL;
+  for (cudaStream_t st : s->streams) {   // the work already enqueued by the worker
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      g_last_cuda_error = static_cast<int>(e);
+      cudaGetLastError();
+      return MXG_ECUDA;
+    }
+  }
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(s->dev_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    g_last_cuda_error = static_cast<int>(e);
+    cudaGetLastError();
+    return MXG_ECUDA;
+  }
+  *flag = v;
+  return MXG_OK;
+}
+
 double mxg_server_now(mxg_server s) { return s ? s->now() : 0.0; }
 
 int mxg_server_destroy(mxg_server s) {

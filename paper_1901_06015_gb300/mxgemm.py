@@ -121,6 +121,8 @@ def lib():
             L.mxg_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
             L.mxg_server_now.restype = _dbl
             L.mxg_server_now.argtypes = [_vp]
+            L.mxg_server_check_device_error.restype = _i32
+            L.mxg_server_check_device_error.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.mxg_server_destroy.restype = _i32
             L.mxg_server_destroy.argtypes = [_vp]
             L.mxg_set_phase_timing.restype = _i32
@@ -425,6 +427,15 @@ class Server:
 
     def now(self):
         return lib().mxg_server_now(self.s)
+
+    def check_device_error(self):
+        """The server's device error word (nonzero: a device-side wait of a served
+        request ran out), cleared by the read."""
+        flag = _i32(0)
+        st = lib().mxg_server_check_device_error(self.s, ctypes.byref(flag))
+        if st:
+            raise MxgError(st, "mxg_server_check_device_error")
+        return flag.value
 
     def close(self):
         if getattr(self, "s", None):

@@ -26,7 +26,9 @@ def test_served_results_equal_alone_and_oracle():
     srv.drain(120)
     comps = srv.poll(10000)
     st = srv.stats()
+    derr = srv.check_device_error()    # no device-side wait ran out
     srv.close()
+    assert derr == 0
     assert len(comps) == len(probs) and all(c["status"] == 0 for c in comps)
     assert st["completed"] == len(probs) and st["failed"] == 0
     assert st["peak_bytes_in_flight"] <= budget or st["max_in_flight"] == 1
