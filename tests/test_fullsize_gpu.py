@@ -1,7 +1,6 @@
 """Parity at the full benchmark size (GPU): m = n = k = 8192, column-major, no
 transpose, U[-1, 1], alpha = beta = 1, in the launch configuration the benchmark times
-(FFMA for single, DMMA for double; one combo per domain case and computation
-precision). The oracle checks 4 sampled 64 x 64 blocks of C (two corners and two
+(FFMA for single, DMMA for double), for all 128 combinations. The oracle checks 4 sampled 64 x 64 blocks of C (two corners and two
 seeded positions); a block obeys C_blk := alpha A(rows, :) B(:, cols) + beta C_blk, so
 the bound uses the block's own operand norms."""
 import numpy as np
@@ -9,7 +8,7 @@ import pytest
 
 from oracle import oracle_mxgemm
 from tests._helpers import normwise_error, tolerance
-from tests.test_parity_gpu import REPS
+from tests.test_parity_gpu import ALL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -18,7 +17,7 @@ N = 8192
 BS = 64
 
 
-@pytest.mark.parametrize("combo", REPS)
+@pytest.mark.parametrize("combo", ALL)
 def test_full_size_sampled_blocks(combo):
     import paper_1901_06015_gb300 as mx
     from paper_1901_06015_gb300 import synth
