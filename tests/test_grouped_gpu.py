@@ -172,3 +172,41 @@ def test_every_grouped_kernel_equals_solo(tmp_path, method_d, variant, solo_d, v
     for p, (_, _, dC) in zip(probs, dev):
         assert np.array_equal(dC.cpu().numpy(), _solo(p, method_d=solo_d)), (p["combo"], p["ta"], p["tb"])
     g.close()
+
+
+def test_grouped_batching_configuration_sampled_blocks():
+    """The batching configuration at its full size, in the launch configuration the
+    benchmark times: 2048 problems, m, n, k = round(exp(U(ln 16, ln 1024))), combination
+    uniform over the 128, entries U[-1, 1], alpha = 1.5, beta = -0.5, one autotuned,
+    graph-captured grouped launch. Every problem is checked against the oracle on a
+    block of up to 16 x 16 entries of C at seeded rows and columns (the block obeys
+    C_blk := alpha A(rows, :) B(:, cols) + beta C_blk, so the bound uses its own norms)."""
+    import paper_1901_06015_gb300 as mx
+    from paper_1901_06015_gb300 import synth
+    rng = np.random.default_rng(0)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    combos = synth.all_combos()
+    items, metas = [], []
+    for _ in range(2048):
+        combo = combos[int(rng.integers(len(combos)))]
+        m, n, k = (int(round(float(np.exp(rng.uniform(np.log(16), np.log(1024)))))) for _ in range(3))
+        A = synth.torch_matrix(gen, m, k, combo[1], "cuda")
+        B = synth.torch_matrix(gen, k, n, combo[2], "cuda")
+        C = synth.torch_matrix(gen, m, n, combo[0], "cuda")
+        items.append(("n", "n", 1.5, A, B, -0.5, C, combo[3]))
+        rows = torch.as_tensor(np.sort(rng.choice(m, size=min(m, 16), replace=False)), device="cuda")
+        cols = torch.as_tensor(np.sort(rng.choice(n, size=min(n, 16), replace=False)), device="cuda")
+        metas.append((combo, k, rows, cols, C[rows][:, cols].cpu().numpy()))
+    g = mx.Group(items, tune=True, graph=True)
+    g.run()
+    torch.cuda.synchronize()
+    assert {b["precision"] for b in g.describe()["buckets"]} == {"s", "d"}
+    for (_, _, _, A, B, _, C, _), (combo, k, rows, cols, C0) in zip(items, metas):
+        Ab = A[rows].cpu().numpy()
+        Bb = B[:, cols].cpu().numpy()
+        got = C[rows][:, cols].cpu().numpy()
+        ref = oracle_mxgemm("n", "n", 1.5, Ab, Bb, -0.5, np.array(C0, order="F"), comp=combo[3])
+        err, _ = normwise_error(combo, got, ref, Ab, Bb, C0, 1.5, -0.5)
+        assert err <= tolerance(combo, k), (combo, k, err)
+    g.close()
