@@ -75,3 +75,44 @@ def test_invalid_request_completes_with_its_status():
     comps = srv.poll()
     srv.close()
     assert comps[0]["id"] == rid and comps[0]["status"] == 2
+
+
+def test_serving_configuration_sampled_blocks():
+    """Requests drawn as the serving configuration draws them (m, n, k log-uniform in
+    [32, 4096], combination uniform over the 128, alpha and beta uniform in [-2, 2]),
+    submitted back to back to a 4-stream server with admission by HBM footprint; A and
+    B are views of shared operand pools, every request has its own C. Each result is
+    checked against the oracle on a block of up to 16 x 16 entries of C."""
+    import paper_1901_06015_gb300 as mx
+    from paper_1901_06015_gb300 import synth
+    rng = np.random.default_rng(2)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2)
+    pool_a = {dt: synth.torch_matrix(gen, 4096, 4096, dt, "cuda") for dt in "sdcz"}
+    pool_b = {dt: synth.torch_matrix(gen, 4096, 4096, dt, "cuda") for dt in "sdcz"}
+    combos = synth.all_combos()
+    srv = mx.Server(n_streams=4, hbm_budget_bytes=8 << 30, small_flops=2e8)
+    reqs = []
+    for _ in range(300):
+        combo = combos[int(rng.integers(len(combos)))]
+        m, n, k = (int(round(float(np.exp(rng.uniform(np.log(32), np.log(4096)))))) for _ in range(3))
+        al, be = float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2))
+        A, B = pool_a[combo[1]][:m, :k], pool_b[combo[2]][:k, :n]
+        C = synth.torch_matrix(gen, m, n, combo[0], "cuda")
+        rows = torch.as_tensor(np.sort(rng.choice(m, size=min(m, 16), replace=False)), device="cuda")
+        cols = torch.as_tensor(np.sort(rng.choice(n, size=min(n, 16), replace=False)), device="cuda")
+        C0 = C[rows][:, cols].cpu().numpy()
+        srv.submit(("n", "n", al, A, B, be, C, combo[3]), keep=(A, B))
+        reqs.append((combo, k, al, be, A, B, C, rows, cols, C0))
+    srv.drain(600)
+    comps = srv.poll(1000)
+    derr = srv.check_device_error()
+    srv.close()
+    assert derr == 0 and len(comps) == len(reqs) and all(c["status"] == 0 for c in comps)
+    torch.cuda.synchronize()
+    for combo, k, al, be, A, B, C, rows, cols, C0 in reqs:
+        Ab, Bb = A[rows].cpu().numpy(), B[:, cols].cpu().numpy()
+        got = C[rows][:, cols].cpu().numpy()
+        ref = oracle_mxgemm("n", "n", al, Ab, Bb, be, np.array(C0, order="F"), comp=combo[3])
+        err, _ = normwise_error(combo, got, ref, Ab, Bb, C0, al, be)
+        assert err <= tolerance(combo, k), (combo, k, err)
