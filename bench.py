@@ -94,7 +94,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -105,10 +105,17 @@ class ClockSampler:
                 smax = float(f[2])
             except ValueError:
                 continue
+            try:
+                power.append(float(f[3].split()[0]))
+            except (ValueError, IndexError):
+                pass
             for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        srt = sorted(sm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "sm_mhz_p10": srt[len(srt) // 10] if srt else None,
+                "power_w_max": max(power) if power else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -462,6 +469,8 @@ def run_precision(args):
     methods = ["ffma", "tf32x3", "bf16x3"]
     results = []
     gen = torch.Generator(device=dev)
+    sampler = ClockSampler(0)
+    sampler.start()
     for dist in ("uniform", "loguniform"):
         for n in sizes:
             for combo in PRECISION_COMBOS:
@@ -486,6 +495,7 @@ def run_precision(args):
                     print(json.dumps(results[-1]), file=sys.stderr, flush=True)
                 del A, B, C0, C
                 torch.cuda.empty_cache()
+    clocks = sampler.stop()
     speed = {}
     for r in results:
         speed.setdefault(r["method"], []).append(r["gflops"])
@@ -496,7 +506,7 @@ def run_precision(args):
                        + args.sizes + ", uniform U[-1,1] and log-uniform sign*10^U(-4,4); best of "
                        + str(args.reps) + " (the call includes its pack kernels)"},
             "geomean_gflops": gm, "speedup_vs_ffma": {m: gm[m] / gm["ffma"] for m in gm},
-            "results": results}
+            "clocks": clocks, "results": results}
     print(json.dumps(line))
     return 0
 
