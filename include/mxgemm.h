@@ -222,7 +222,7 @@ int mxg_check_device_error(mxg_handle h, int* flag);
  * grouped pack launch and one persistent contraction launch per bucket (plus a
  * C := beta*C launch per problem with k == 0 or alpha == 0).
  *   method_s: MXG_METHOD_AUTO or MXG_METHOD_FFMA (single-precision bucket);
- *   method_d: MXG_METHOD_AUTO, MXG_METHOD_DMMA or MXG_METHOD_DFMA (double bucket);
+ *   method_d: MXG_METHOD_AUTO (= DFMA), MXG_METHOD_DMMA or MXG_METHOD_DFMA (double bucket);
  *   flags:    MXG_GROUP_TUNE  -- time each bucket's candidate kernels and schedules
  *                                 (into scratch copies of C, so the problems' C are not
  *                                 touched) and keep the fastest; decisions are cached in

@@ -89,10 +89,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // thread copies TK/8 vectors -- H elements, 16, 8 or 4 bytes -- of A' and as many of B'
 // per k-tile; each row of a k-tile is TM elements = 32 threads' vectors), so the loads
 // for k-tile kt + S - 1 are in flight while k-tile kt is computed.
+// ncols: columns of the tile inside the real product (the rest is padding). With H = 1
+// warp w owns tile columns 4w .. 4w+3 (threads 32w .. 32w+31 have tn = 2w, 2w+1), so a
+// warp whose columns all lie in the padding skips its FMAs: those outputs are never
+// stored, and it still takes part in the copies and barriers.
 template <typename T, int H, int TK, int S>
 __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* __restrict__ B, int64_t lda,
                                               int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
-                                              SimtSmem<T, H, TK, S>& sm, T (&acc)[2 * H][2 * H]) {
+                                              SimtSmem<T, H, TK, S>& sm, T (&acc)[2 * H][2 * H],
+                                              int64_t ncols = 32 * H) {
   using V = typename VecT<T, H>::V;
   constexpr int TM = 32 * H, R = 2 * H;
   constexpr int CP = TK / 8;                          // rows each thread copies per operand and k-tile
@@ -134,6 +139,7 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
     }
     cp_async_commit();
     const int buf = static_cast<int>(kt % S);
+    if (H == 1 && 4 * static_cast<int64_t>(tid >> 5) >= ncols) continue;   // whole warp in the padding
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
       T a[R], b[R];
@@ -232,7 +238,9 @@ simt_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restri
     const GroupProb& p = probs[tl.prob];
     const int64_t m0 = static_cast<int64_t>(tl.tm) * 32 * H, n0 = static_cast<int64_t>(tl.tn) * 32 * H;
     __syncthreads();   // the previous tile's shared-memory reads are done
-    simt_mainloop<T, H>(static_cast<const T*>(p.A), static_cast<const T*>(p.B), p.lda, p.ldb, p.Kp, m0, n0, sm, acc);
+    const int64_t nreal = p.e.n * (p.mode == OUT_COLPAIR ? 2 : 1);   // columns of the real product
+    simt_mainloop<T, H>(static_cast<const T*>(p.A), static_cast<const T*>(p.B), p.lda, p.ldb, p.Kp, m0, n0, sm, acc,
+                        nreal - n0);
     simt_epilogue_rt<T, H>(p.cdt, p.mode, p.e, m0, n0, acc);
   }
 }

@@ -257,10 +257,11 @@ int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int metho
   bs.plan_method = MXG_METHOD_FFMA;
   bs.candidates = {VAR_FFMA_128, VAR_FFMA_64, VAR_FFMA_32};
   bd.comp_double = 1;
-  bd.plan_method = (method_d == MXG_METHOD_DFMA) ? MXG_METHOD_DFMA : MXG_METHOD_DMMA;
-  bd.candidates = (method_d == MXG_METHOD_AUTO)   ? std::vector<int>{VAR_DMMA_64, VAR_DFMA_64, VAR_DFMA_32}
-                  : (method_d == MXG_METHOD_DMMA) ? std::vector<int>{VAR_DMMA_64}
-                                                  : std::vector<int>{VAR_DFMA_64, VAR_DFMA_32};
+  // AUTO means DFMA for double precision, as in a single call (faster than DMMA on this
+  // chip); planning with the DFMA tile pads K' to 8 instead of the DMMA kernel's 16
+  bd.plan_method = (method_d == MXG_METHOD_DMMA) ? MXG_METHOD_DMMA : MXG_METHOD_DFMA;
+  bd.candidates = (method_d == MXG_METHOD_DMMA) ? std::vector<int>{VAR_DMMA_64}
+                                                : std::vector<int>{VAR_DFMA_32, VAR_DFMA_64};
   g->plans.resize(static_cast<size_t>(count));
   for (int64_t i = 0; i < count; ++i) {
     const mxg_problem& q = probs[i];

@@ -72,8 +72,8 @@ def test_grouped_equals_solo_and_oracle(tune, graph):
 
 
 def test_grouped_auto_double_kernel_within_tolerance_and_replay():
-    """method_d = auto lets the tuner pick DMMA or DFMA; two graph replays equal two
-    solo applications (beta != 0, so each run changes C)."""
+    """method_d = auto (DFMA kernels, tile chosen by the tuner); two graph replays equal
+    two solo applications (beta != 0, so each run changes C)."""
     import paper_1901_06015_gb300 as mx
     probs = _problems(2, 64, trans=False)
     items, dev = _device_items(probs)
