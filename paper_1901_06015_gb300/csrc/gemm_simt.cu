@@ -222,7 +222,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmA
   __shared__ SimtSmem<T, H, PlainTile<T, H>::TK, PlainTile<T, H>::S> sm;
   T acc[2 * H][2 * H];
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 32 * H, n0 = static_cast<int64_t>(blockIdx.y) * 32 * H;
-  simt_mainloop<T, H>(static_cast<const T*>(g.A), static_cast<const T*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, sm, acc);
+  const int64_t nreal = g.e.n * (MODE == OUT_COLPAIR ? 2 : 1);   // columns of the real product
+  simt_mainloop<T, H>(static_cast<const T*>(g.A), static_cast<const T*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, sm, acc,
+                      nreal - n0);
   simt_epilogue<T, H, CDT, MODE>(g.e, m0, n0, acc);
 }
 
@@ -341,8 +343,16 @@ int variant_tile(int variant) {
 
 cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, cudaStream_t s) {
   const TileCfg t = tile_cfg(method);
-  const int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
+  int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
+  if (method == MXG_METHOD_DFMA) {
+    // DFMA runs 32 x 32 tiles over the real product's extent inside the 64-padded packs:
+    // the FP64 pipe is busy with a few warps per SM, so smaller tiles only cut padding
+    const int64_t mr = g.e.m * (mode == OUT_ROWPAIR ? 2 : 1), nr = g.e.n * (mode == OUT_COLPAIR ? 2 : 1);
+    gx = (mr + 31) / 32;
+    gy = (nr + 31) / 32;
+    if (gx <= 0 || gy <= 0) return cudaSuccess;
+  }
   if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   if (method == MXG_METHOD_DMMA) return launch_dmma(mode, c_dt, g, s, grid);
@@ -350,7 +360,7 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
   const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto M) {
     constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
     if (method == MXG_METHOD_FFMA) simt_gemm<float, 4, CDT, MODE><<<grid, 256, 0, s>>>(g);
-    else simt_gemm<double, 2, CDT, MODE><<<grid, 256, 0, s>>>(g);
+    else simt_gemm<double, 1, CDT, MODE><<<grid, 256, 0, s>>>(g);
   });
   return ok ? cudaGetLastError() : cudaErrorInvalidValue;
 }
