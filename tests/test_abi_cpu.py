@@ -109,3 +109,33 @@ def test_empty_operands_accept_any_strides():
 def test_empty_C_accepts_any_strides():
     info = mx.mxg_plan("dddd", 0, 4, 3, strides=((0, 0), (1, 3), (0, 0)))
     assert info.flops == 0
+
+
+def test_tune_file_round_trip(tmp_path):
+    """The autotuner's decision file (host only, no CUDA call): mxg_tune_load keeps the
+    lines with a known kernel variant (0..5) and schedule (0 dynamic, 1 static) and drops
+    the rest; mxg_tune_save writes back exactly what is held."""
+    src = tmp_path / "in.txt"
+    src.write_text("\n".join([
+        "d1-m5-c0-n20-f71-k16 3 0 48.6",     # DFMA 32 x 32, dynamic
+        "d0-m1-c0-n20-f71-k16 1 1 1.78",     # FFMA 64 x 64, static
+        "d0-m1-c0-n9-f40-k10 5 0 0.25",      # FFMA 32 x 32
+        "bad-variant 9 0 1.0",               # no such kernel
+        "bad-schedule 2 7 1.0",              # no such schedule
+    ]) + "\n")
+    assert mx.mxg_tune_load(str(src)) == 0
+    out = tmp_path / "out.txt"
+    assert mx.mxg_tune_save(str(out)) == 0
+    held = {}
+    for line in out.read_text().splitlines():
+        sig, v, sch, ms = line.split()
+        held[sig] = (int(v), int(sch), float(ms))
+    assert held["d1-m5-c0-n20-f71-k16"] == (3, 0, pytest.approx(48.6))
+    assert held["d0-m1-c0-n20-f71-k16"] == (1, 1, pytest.approx(1.78))
+    assert held["d0-m1-c0-n9-f40-k10"] == (5, 0, pytest.approx(0.25))
+    assert "bad-variant" not in held and "bad-schedule" not in held
+
+
+def test_tune_file_errors(tmp_path):
+    assert mx.mxg_tune_load(str(tmp_path / "missing.txt")) == 1     # MXG_EINVAL
+    assert mx.mxg_tune_save(str(tmp_path / "no-such-dir" / "x.txt")) == 1
