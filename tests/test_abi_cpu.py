@@ -139,3 +139,35 @@ def test_tune_file_round_trip(tmp_path):
 def test_tune_file_errors(tmp_path):
     assert mx.mxg_tune_load(str(tmp_path / "missing.txt")) == 1     # MXG_EINVAL
     assert mx.mxg_tune_save(str(tmp_path / "no-such-dir" / "x.txt")) == 1
+
+
+def test_binding_marshals_layouts_and_datatypes():
+    """The Python binding only marshals: a tensor becomes (pointer, datatype code,
+    row stride, column stride) in elements of its datatype; a (rows, cols, 2) binary16 /
+    bfloat16 tensor is one complex matrix with halved strides; m, n, k come from C and
+    op(A). Checked on CPU tensors (no CUDA call)."""
+    torch = pytest.importorskip("torch")
+    A = torch.zeros(6, 4, dtype=torch.complex64)                      # row-major c
+    B = torch.zeros(5, 6, dtype=torch.float64).t()                    # column-major d, 6 x 5
+    C = torch.zeros(9, 13, dtype=torch.float32)[::2, ::3]             # general s, 5 x 5
+    arr, n = mx.make_problems([("t", "c", 1.5 - 0.5j, A, B, -0.25, C, "d")])
+    p = arr[0]
+    assert n == 1
+    assert (p.transa, p.transb, p.m, p.n, p.k) == (1, 2, 5, 5, 6)
+    assert (p.alpha_re, p.alpha_im, p.beta_re, p.beta_im) == (1.5, -0.5, -0.25, 0.0)
+    assert (p.dtA, p.rsA, p.csA) == (2, 4, 1)
+    assert (p.dtB, p.rsB, p.csB) == (1, 1, 6)
+    assert (p.dtC, p.rsC, p.csC) == (0, 26, 3)
+    assert p.A == A.data_ptr() and p.B == B.data_ptr() and p.C == C.data_ptr()
+    assert p.comp_prec == 1
+    # complex binary16 / bfloat16 as (rows, cols, 2), column-major over (rows, cols)
+    K = torch.zeros(7, 3, 2, dtype=torch.float16).permute(1, 0, 2)    # 3 x 7 complex, strides (2, 6, 1)
+    W = torch.zeros(3, 7, 2, dtype=torch.bfloat16)                    # 3 x 7 complex, row-major
+    H = torch.zeros(7, 7, dtype=torch.float16)
+    arr, _ = mx.make_problems([("n", "n", 1.0, K, H, 0.0, W, "h")])
+    p = arr[0]
+    assert (p.dtA, p.rsA, p.csA) == (5, 1, 3)
+    assert (p.dtC, p.rsC, p.csC) == (7, 7, 1)
+    assert (p.dtB, p.m, p.n, p.k, p.comp_prec) == (4, 3, 7, 7, 3)
+    with pytest.raises(TypeError):
+        mx.make_problems([("n", "n", 1.0, torch.zeros(2, 2, dtype=torch.int32), H, 0.0, H, "s")])
