@@ -138,11 +138,21 @@ __device__ __forceinline__ void dmma_epilogue_rt(int cdt, int mode, const EpiArg
   with_c_mode(cdt, mode, [&](auto C, auto M) { dmma_epilogue<decltype(C)::value, decltype(M)::value>(e, m0, n0, Cs); });
 }
 
+// Blocks are numbered in launch order (x fastest) and mapped to tiles in groups of
+// DM_GM tile rows, columns of the group next: the blocks resident at one time then
+// cover a few tile rows and a few tile columns, whose packed panels they share in L2.
+constexpr int DM_GM = 16;
+
 template <int CDT, int MODE>
 __global__ void __launch_bounds__(128) dmma_gemm(GemmArgs g) {
   __shared__ __align__(16) double smem[DM_SMEM];
   double acc[4][4][2];
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * DM_T, n0 = static_cast<int64_t>(blockIdx.y) * DM_T;
+  const int64_t tiles_m = gridDim.x, tiles_n = gridDim.y;
+  const int64_t bid = static_cast<int64_t>(blockIdx.y) * tiles_m + blockIdx.x;
+  const int64_t per_group = DM_GM * tiles_n;
+  const int64_t gm0 = (bid / per_group) * DM_GM, r = bid % per_group;
+  const int64_t gsz = (tiles_m - gm0 < DM_GM) ? tiles_m - gm0 : DM_GM;
+  const int64_t m0 = (gm0 + r % gsz) * DM_T, n0 = (r / gsz) * DM_T;
   dmma_mainloop(static_cast<const double*>(g.A), static_cast<const double*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, smem, acc);
   dmma_stage(smem, acc);
   dmma_epilogue<CDT, MODE>(g.e, m0, n0, smem);
