@@ -96,9 +96,23 @@ enum {
   MXG_ECUDA = 4,           /* a CUDA runtime call failed (see mxg_last_cuda_error) */
   MXG_ETIMEOUT = 5,        /* a device-side wait ran out of its iteration limit */
   MXG_ENOTSUP = 6,         /* method not available on this device */
-  MXG_ESCRATCH = 7         /* mxgemm_noalloc: the call needs more scratch than the fixed
+  MXG_ESCRATCH = 7,        /* mxgemm_noalloc: the call needs more scratch than the fixed
                               MXG_NOALLOC_SCRATCH_BYTES buffer holds */
+  MXG_EACCURACY = 8        /* the split-precision method cannot keep the normwise error
+                              within 4 k u_s at this k (see MXG_SPLIT_MIN_K_*) */
 };
+
+/* Smallest k at which a split-precision method is accepted. Its products drop terms of
+ * relative size up to 3 u_p^2 (u_p the unit roundoff of the plane format: 2^-8 for
+ * BF16, 2^-11 for TF32), a floor independent of k. The stated accuracy is a normwise
+ * error of at most 4 k u_s (u_s = 2^-24), so below some k the floor alone can exceed
+ * it. The limits leave room for the floor (774 u_s for BF16X3, 12 u_s for TF32X3),
+ * the FP32 accumulation on the tensor cores (taken as at most 4 u_s per MMA step on
+ * the sum of magnitudes, 3 K'/16 resp. 3 K'/8 steps with K' <= 2k) and the epilogue's
+ * roundings (about 5.5 u_s): BF16X3 needs 2.5 k >= 780, TF32X3 k >= 18. A call below
+ * the limit returns MXG_EACCURACY and enqueues nothing; FFMA and TF32X3 cover it. */
+#define MXG_SPLIT_MIN_K_BF16X3 320
+#define MXG_SPLIT_MIN_K_TF32X3 32
 
 /* Domain cases of Fig. "mixeddom", as returned in mxg_plan_info.domain_case:
  * index = 4*[C complex] + 2*[A complex] + [B complex]. */
@@ -274,11 +288,18 @@ int mxg_tune_load(const char* path);
  * streams and overlaps on the device: requests of at most small_flops useful flops go
  * to a high-priority stream, larger ones round-robin over the others (flag
  * MXG_SERVE_FIFO instead sends every request to stream 0 in submission order, with no
- * priority, which is the serial baseline). When the head of the queue does not fit,
- * later small requests that fit are admitted past it. Completion is observed with one
- * CUDA event per request; times are seconds on the server's clock (mxg_server_now):
- * arrival = when submitted, admit = when enqueued, done = when the request's last
- * kernel finished on the device.
+ * priority, which is the serial baseline). Small requests are batched: those admitted
+ * while the previous wave still runs on the high-priority stream wait for it to finish
+ * and then run together as one wave -- one grouped pack launch and one persistent
+ * grouped contraction per computation precision over all of their tiles (the kernels of
+ * mxg_group_run, so each result equals the separate call's bit for bit). Plain
+ * FFMA / DFMA / DMMA requests join waves; a request on the split-precision or 16-bit
+ * tensor-core methods, or C := beta*C only, runs on its own. When the head of the queue
+ * does not fit, later small requests that fit are admitted past it, until the head has
+ * waited 50 ms. Completion is observed with one CUDA event per wave or request; times
+ * are seconds on the server's clock (mxg_server_now): arrival = when submitted, admit =
+ * when its memory was reserved, done = when the request's last kernel finished on the
+ * device.
  */
 typedef struct mxg_server_s* mxg_server;
 
@@ -295,6 +316,7 @@ typedef struct {
   uint64_t submitted, admitted, completed, failed;
   size_t bytes_in_flight, peak_bytes_in_flight, budget;
   int64_t max_in_flight, queue_len;
+  uint64_t waves, wave_requests;   /* grouped launches of small requests, and the requests they held */
 } mxg_server_stats;
 
 enum { MXG_SERVE_FIFO = 1 };
@@ -329,9 +351,10 @@ int mxg_phase_times(mxg_handle h, double* pack_ms, double* contraction_ms, int64
 /*
  * mxgemm_noalloc: mxgemm_ex without any device allocation. (The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc:
- * work enqueued while a stream is captured into a CUDA graph, latency-critical loops
- * that cannot take the implicit synchronisation of cudaMalloc/cudaFree, and
- * applications whose device memory is all owned by another allocator.)
+ * latency-critical loops that cannot take the implicit device synchronisation of
+ * cudaMalloc/cudaFree, and applications whose device memory is all owned by another
+ * allocator -- a framework's caching pool or a fixed memory plan -- that forbids side
+ * allocations.)
  *
  * Same arguments and semantics as mxgemm_ex, with a cudaStream_t (NULL = legacy
  * default stream) in place of the handle. The packed operands live in one fixed
@@ -339,12 +362,18 @@ int mxg_phase_times(mxg_handle h, double* pack_ms, double* contraction_ms, int64
  * loads this code holds until the process exits; the call makes no cudaMalloc,
  * cudaFree or other allocating call. A problem whose packed operands need more than
  * that (see mxg_plan's workspace_bytes) is rejected with MXG_ESCRATCH and nothing is
- * enqueued. The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream capture.
- * All calls in the process share the one array and it keeps the last call's contents
- * (every call rewrites all of the part it uses, so nothing needs clearing), so calls
- * whose work may overlap on the GPU -- on different streams, or from several host
- * threads -- race on it: serialise them on one stream.
+ * enqueued. The first call on a device (or the first mxgemm_noalloc_check_device_error
+ * there) looks up the array's device address, once per device, with that device
+ * current. All calls in the process share the one array and it keeps the last call's
+ * contents (every call rewrites all of the part it uses, so nothing needs clearing),
+ * so calls whose work may overlap on the GPU -- on different streams, or from several
+ * host threads -- race on it: serialise them on one stream.
+ *
+ * Timeouts: the tensor-core methods (TF32X3, BF16X3, TC16) bound every device-side
+ * wait; a wait that runs out makes the kernel skip its stores and set this entry
+ * point's own device error word (a second file-scope device int, shared by all calls
+ * like the array). The call itself has returned MXG_OK by then, so check the word with
+ * mxgemm_noalloc_check_device_error after the work.
  */
 #define MXG_NOALLOC_SCRATCH_BYTES (32u << 20)
 int mxgemm_noalloc(void* stream, int method, int transa, int transb,
@@ -355,6 +384,13 @@ int mxgemm_noalloc(void* stream, int method, int transa, int transb,
                    double beta_re, double beta_im,
                    void* C, int dtC, int64_t rsC, int64_t csC,
                    int comp_prec);
+
+/* The device error word of mxgemm_noalloc on the current device: synchronises
+ * `stream` (a cudaStream_t, NULL = legacy default stream), writes the word to *flag
+ * (nonzero: a device-side wait of some mxgemm_noalloc call ran out of its limit since
+ * the word was last cleared) and clears it. Allocates nothing. Returns MXG_OK or
+ * MXG_ECUDA. */
+int mxgemm_noalloc_check_device_error(void* stream, int* flag);
 
 /* Self-test of the device-side wait limit: launches one kernel that waits on an
  * mbarrier nothing will ever arrive on, for at most `seconds` (0 < seconds <= 10), on

@@ -131,6 +131,11 @@ int make_plan(const Call& c, int method, Plan* p) {
   P.real_products = 1;
   if (c.m == 0 || c.n == 0) { P.kind = PLAN_NOOP; return MXG_OK; }
   if (c.k == 0 || P.alpha_zero) { P.kind = PLAN_SCALE; return MXG_OK; }
+  // The split products' error floor (3 u_p^2 per product, independent of k) must fit
+  // the accuracy 4 k u_s with the accumulation and the epilogue (include/mxgemm.h).
+  if ((method == MXG_METHOD_BF16X3 && c.k < MXG_SPLIT_MIN_K_BF16X3) ||
+      (method == MXG_METHOD_TF32X3 && c.k < MXG_SPLIT_MIN_K_TF32X3))
+    return MXG_EACCURACY;
   P.kind = PLAN_GEMM;
 
   // Sec. 2.2.5: compute C^T := op(B)^T op(A)^T when C is row-stored, so the epilogue
@@ -353,6 +358,7 @@ const char* mxg_strerror(int status) {
     case MXG_ETIMEOUT: return "device-side wait ran out of its iteration limit";
     case MXG_ENOTSUP: return "method not supported on this device";
     case MXG_ESCRATCH: return "problem needs more scratch than the fixed no-allocation buffer (MXG_NOALLOC_SCRATCH_BYTES) holds";
+    case MXG_EACCURACY: return "split-precision method cannot meet the accuracy 4*k*u_s at this k (BF16X3 needs k >= 320, TF32X3 k >= 32)";
   }
   return "unknown status";
 }

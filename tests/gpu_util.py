@@ -84,9 +84,13 @@ def run(combo, A, B, C, alpha, beta, transa="n", transb="n", method="auto"):
     return from_device(dC, combo[0])
 
 
-def methods_for(combo):
-    from tests._helpers import comp_prec
+def methods_for(combo, k=None):
+    """Methods of combo's computation precision; with k given, only those the planner
+    accepts at that k (the split-precision methods have a smallest k)."""
+    from tests._helpers import comp_prec, SPLIT_MIN_K
     x = comp_prec(combo)
     if x in ("h", "b"):
         return ["tc16"]
-    return ["ffma", "tf32x3", "bf16x3"] if x == "s" else ["dmma", "dfma"]
+    if x == "d":
+        return ["dmma", "dfma"]
+    return [m for m in ("ffma", "tf32x3", "bf16x3") if k is None or k >= SPLIT_MIN_K.get(m, 0)]

@@ -25,10 +25,10 @@ def test_16bit_parity(combo):
     beta = (-0.5 + 0.25j) if synth.is_complex(combo[0]) else -0.5
     ref_C = C0.copy()
     ref = oracle_mxgemm("n", "n", alpha, A, B, beta, ref_C, comp=combo[3])
-    for meth in methods_for(combo):
+    for meth in methods_for(combo, k):
         got = run(combo, A, B, C0, alpha, beta, method=meth)
         err, _ = normwise_error(combo, got, ref, A, B, C0, alpha, beta)
-        assert err <= tolerance(combo, k, meth), (combo, meth, err, tolerance(combo, k, meth))
+        assert err <= tolerance(combo, k, meth, beta), (combo, meth, err, tolerance(combo, k, meth, beta))
 
 
 @pytest.mark.parametrize("combo", ALL_16)
@@ -45,7 +45,7 @@ def test_16bit_small_integers_bit_exact(combo):
     for alpha, beta in ((1.0, 0.0), (-2.0, 1.0), (1.0, -0.5)):
         ref_C = C0.copy()
         oracle_mxgemm("n", "n", alpha, A, B, beta, ref_C, comp=combo[3])
-        for meth in methods_for(combo):
+        for meth in methods_for(combo, k):
             got = run(combo, A, B, C0, alpha, beta, method=meth)
             assert np.array_equal(synth.to_c128(got), synth.to_c128(ref_C)), (combo, meth, alpha, beta)
 

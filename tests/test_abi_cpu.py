@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_strerror_codes():
-    for st in range(8):
+    for st in range(9):
         assert mx.mxg_strerror(st) and "unknown" not in mx.mxg_strerror(st)
 
 
@@ -98,6 +98,27 @@ def test_imaginary_alpha_status(combo):
     mx.mxg_plan(combo[:3] + combo[3], 4, 4, 4, alpha=2.0)
     mx.mxg_plan("zzzd", 4, 4, 4, alpha=1 + 1j)
     mx.mxg_plan("dddd", 4, 4, 4, alpha=1 + 1j)
+
+
+def test_split_methods_have_a_smallest_k():
+    """The split-precision methods are planned only where their error floor (3 u_p^2
+    per product) leaves the stated bound 4 k u_s room for the accumulation and the
+    epilogue: BF16x3 from k = 320, TF32x3 from k = 32 (MXG_EACCURACY = 8 below). The
+    header's numbers follow from the floor: 2.5 k >= 3 * 2^8 (1 + 2^-7) + 5.5 and
+    k >= 12 (1 + 2^-10) + 5.5 in units of 2^-24, rounded up."""
+    floor_bf16 = 3 * 2 ** 8 * (1 + 2 ** -7)
+    floor_tf32 = 3 * 2 ** 2 * (1 + 2 ** -10)
+    assert 2.5 * 320 >= floor_bf16 + 5.5 > 2.5 * 300
+    assert 32 >= floor_tf32 + 5.5
+    for combo in ("ssss", "zzzs", "dsss", "csss", "zcds"):
+        for meth, kmin in (("bf16x3", 320), ("tf32x3", 32)):
+            with pytest.raises(mx.MxgError) as e:
+                mx.mxg_plan(combo, 64, 64, kmin - 1, method=meth)
+            assert e.value.status == 8
+            assert mx.mxg_plan(combo, 64, 64, kmin, method=meth).method == mx.METHODS[meth]
+        # quick returns need no accuracy: k == 0 is C := beta C
+        assert mx.mxg_plan(combo, 64, 64, 0, method="bf16x3").flops == 0
+        assert mx.mxg_plan(combo, 64, 64, 1, method="ffma").flops > 0
 
 
 def test_empty_operands_accept_any_strides():
