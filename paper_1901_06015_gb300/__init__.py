@@ -6,7 +6,7 @@ The compute path is the CUDA library ``_build/libmxgemm.so`` behind the C ABI in
 marshalling only). There is no CPU fallback: if the library is missing, calls raise.
 """
 from .mxgemm import (  # noqa: F401
-    MxgError, Handle, PlanInfo, Problem, Group, Server, lib, mxgemm, mxgemm_ex, mxgemm_noalloc, mxgemm_grouped,
+    MxgError, Handle, PlanInfo, Problem, Group, Server, lib, mxgemm, mxgemm_ex, mxgemm_noalloc, mxgemm_noalloc_check_device_error, mxgemm_grouped,
     mxg_plan, mxg_tune_save, mxg_tune_load, make_problems, mxg_strerror,
     METHODS, DT_CODES, TRANS_CODES, PREC_CODES, CASE_NAMES, dt_of,
 )

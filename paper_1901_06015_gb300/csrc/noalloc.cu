@@ -1,12 +1,12 @@
 // mxgemm_noalloc: the plain mixed-datatype gemm for callers that must not allocate
-// device memory. Some callers cannot call cudaMalloc: code that enqueues work while a
-// CUDA stream is being captured into a graph (allocation is not a capturable
-// operation), latency-critical loops that cannot afford the implicit device
-// synchronisation of cudaMalloc/cudaFree, and applications whose device memory is all
-// owned by another allocator (a framework's caching pool) that forbids side
+// device memory. Some callers cannot call cudaMalloc: latency-critical loops that
+// cannot afford the implicit device synchronisation of cudaMalloc/cudaFree, and
+// applications whose device memory is all owned by another allocator (a framework's
+// caching pool, an embedded runtime with a fixed memory plan) that forbids side
 // allocations. This entry point runs the same pack and contraction kernels as
 // mxgemm_ex, but its packed operands live in one fixed, file-scope device array of
-// MXG_NOALLOC_SCRATCH_BYTES bytes instead of a cudaMalloc'd workspace.
+// MXG_NOALLOC_SCRATCH_BYTES bytes instead of a cudaMalloc'd workspace, and the error
+// word its tensor-core kernels set on a wait timeout is a file-scope device int.
 #include <mutex>
 
 #include "plan.h"
@@ -20,11 +20,16 @@ using namespace mxg;
 
 // The fixed scratch: every GPU that loads this code holds it until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MXG_NOALLOC_SCRATCH_BYTES];
+// Error word of this entry point: a bounded device-side wait that runs out sets it to 1
+// (the kernel then skips its stores); it stays set until
+// mxgemm_noalloc_check_device_error reads and clears it.
+static __device__ int g_noalloc_err;
 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
+int* g_noalloc_err_ptr[kMaxDevices] = {};
 
 int noalloc_cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MXG_OK;
@@ -32,10 +37,10 @@ int noalloc_cuda_status(cudaError_t e) {
   return MXG_ECUDA;
 }
 
-// Device address of the scratch array on the current device. The name of a
-// __device__ array in host code is only a host-side stand-in, so the address is
-// looked up once per device, with that device current, and cached.
-int scratch_address(void** out) {
+// Device addresses of the scratch array and the error word on the current device. The
+// name of a __device__ variable in host code is only a host-side stand-in, so the
+// addresses are looked up once per device, with that device current, and cached.
+int scratch_address(void** out, int** err) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_cuda_status(e);
@@ -43,11 +48,16 @@ int scratch_address(void** out) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
+    void* q = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) return noalloc_cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_noalloc_err);
+    if (e != cudaSuccess || p == nullptr || q == nullptr)
+      return noalloc_cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+    g_noalloc_err_ptr[dev] = static_cast<int*>(q);
     g_noalloc_ptr[dev] = p;
   }
   *out = g_noalloc_ptr[dev];
+  *err = g_noalloc_err_ptr[dev];
   return MXG_OK;
 }
 }  // namespace
@@ -74,9 +84,31 @@ extern "C" int mxgemm_noalloc(void* stream, int method, int transa, int transb,
   if (P.kind == PLAN_GEMM && P.workspace > static_cast<size_t>(MXG_NOALLOC_SCRATCH_BYTES))
     return MXG_ESCRATCH;
   void* ws = nullptr;
-  st = scratch_address(&ws);
+  int* err = nullptr;
+  st = scratch_address(&ws, &err);
   if (st != MXG_OK) return st;
   // The pack kernels write every byte of the padded packed operands (zeros included),
-  // so nothing left in the scratch by an earlier call needs clearing.
-  return enqueue_plan(P, ws, static_cast<cudaStream_t>(stream), nullptr);
+  // so nothing left in the scratch by an earlier call needs clearing. The error word is
+  // only ever set by a kernel and cleared by the check below.
+  return enqueue_plan(P, ws, static_cast<cudaStream_t>(stream), nullptr, err);
+}
+
+extern "C" int mxgemm_noalloc_check_device_error(void* stream, int* flag) {
+  if (!flag) return MXG_EINVAL;
+  void* ws = nullptr;
+  int* err = nullptr;
+  int st = scratch_address(&ws, &err);
+  if (st != MXG_OK) return st;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && v) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess && v) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return noalloc_cuda_status(e);
+  }
+  *flag = v;
+  return MXG_OK;
 }

@@ -48,7 +48,8 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("failed", ctypes.c_uint64), ("bytes_in_flight", _sz), ("peak_bytes_in_flight", _sz),
-                ("budget", _sz), ("max_in_flight", _i64), ("queue_len", _i64)]
+                ("budget", _sz), ("max_in_flight", _i64), ("queue_len", _i64),
+                ("waves", ctypes.c_uint64), ("wave_requests", ctypes.c_uint64)]
 
 
 class MxgError(RuntimeError):
@@ -94,6 +95,8 @@ def lib():
             L.mxg_check_device_error.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.mxgemm_noalloc.restype = _i32
             L.mxgemm_noalloc.argtypes = [_vp, _i32] + _GEMM_TAIL
+            L.mxgemm_noalloc_check_device_error.restype = _i32
+            L.mxgemm_noalloc_check_device_error.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.mxg_group_create.restype = _i32
             L.mxg_group_create.argtypes = [_vp, _i64, ctypes.POINTER(Problem), _i32, _i32, _i32,
                                            ctypes.POINTER(_vp), ctypes.POINTER(_i64)]
@@ -316,6 +319,20 @@ def mxgemm_noalloc(method, transa, transb, alpha, A, B, beta, C, comp="c", strea
     if st:
         raise MxgError(st, "mxgemm_noalloc")
     return C
+
+
+def mxgemm_noalloc_check_device_error(stream=None):
+    """Read and clear mxgemm_noalloc's device error word on the current device after
+    synchronising ``stream`` (default: torch's current stream); nonzero means a
+    device-side wait of some call ran out of its limit."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ptr = getattr(s, "cuda_stream", s)
+    flag = _i32(0)
+    st = lib().mxgemm_noalloc_check_device_error(ctypes.c_void_p(ptr or 0), ctypes.byref(flag))
+    if st:
+        raise MxgError(st, "mxgemm_noalloc_check_device_error")
+    return int(flag.value)
 
 
 def make_problems(items):
