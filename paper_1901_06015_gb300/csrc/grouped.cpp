@@ -20,6 +20,52 @@ namespace mxg {
 extern thread_local int g_last_cuda_error;
 }
 
+namespace mxg {
+
+std::vector<GroupTile> group_tiles(const std::vector<GroupProb>& probs, int variant) {
+  const int T = variant_tile(variant);
+  std::vector<std::pair<int64_t, GroupTile>> v;
+  for (size_t i = 0; i < probs.size(); ++i) {
+    const GroupProb& p = probs[i];
+    // logical extent of the real product: the epilogue's C extent times the pairing
+    const int64_t Mr = p.e.m * (p.mode == OUT_ROWPAIR ? 2 : 1);
+    const int64_t Nr = p.e.n * (p.mode == OUT_COLPAIR ? 2 : 1);
+    const int tm = static_cast<int>((Mr + T - 1) / T), tn = static_cast<int>((Nr + T - 1) / T);
+    for (int x = 0; x < tm; ++x)
+      for (int y = 0; y < tn; ++y) v.push_back({p.Kp, GroupTile{static_cast<int>(i), x, y}});
+  }
+  std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<GroupTile> out;
+  out.reserve(v.size());
+  for (auto& e : v) out.push_back(e.second);
+  return out;
+}
+
+void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta, PackArgs* tb) {
+  const Call& w = P.work;
+  char* pb = pa + P.bytes_a;
+  *gp = GroupProb{};
+  gp->A = pa; gp->B = pb;
+  gp->lda = P.Mp; gp->ldb = P.Np; gp->Kp = P.Kp;
+  gp->e = plan_epilogue(P);
+  gp->cdt = w.dtC;
+  gp->mode = P.mode;
+  *ta = PackArgs{};
+  ta->src = w.A; ta->src_dt = w.dtA;
+  if (w.transa == MXG_TRANS || w.transa == MXG_CONJTRANS) { ta->smn = w.csA; ta->sk = w.rsA; }
+  else { ta->smn = w.rsA; ta->sk = w.csA; }
+  ta->MN = w.m; ta->K = w.k; ta->pattern = P.pat_a; ta->conj = P.conj_a;
+  ta->dst = pa; ta->ld = P.Mp; ta->MNp = P.Mp; ta->Kp = P.Kp; ta->layout = LAYOUT_MN_MAJOR; ta->split = SPLIT_NONE;
+  *tb = PackArgs{};
+  tb->src = w.B; tb->src_dt = w.dtB;
+  if (w.transb == MXG_TRANS || w.transb == MXG_CONJTRANS) { tb->smn = w.rsB; tb->sk = w.csB; }
+  else { tb->smn = w.csB; tb->sk = w.rsB; }
+  tb->MN = w.n; tb->K = w.k; tb->pattern = P.pat_b; tb->conj = P.conj_b;
+  tb->dst = pb; tb->ld = P.Np; tb->MNp = P.Np; tb->Kp = P.Kp; tb->layout = LAYOUT_MN_MAJOR; tb->split = SPLIT_NONE;
+}
+
+}  // namespace mxg
+
 using namespace mxg;
 
 namespace {
@@ -58,24 +104,7 @@ struct Bucket {
   std::string signature;
 };
 
-std::vector<GroupTile> make_tiles(const Bucket& b, int variant) {
-  const int T = variant_tile(variant);
-  std::vector<std::pair<int64_t, GroupTile>> v;
-  for (size_t i = 0; i < b.probs.size(); ++i) {
-    const GroupProb& p = b.probs[i];
-    // logical extent of the real product: the epilogue's C extent times the pairing
-    const int64_t Mr = p.e.m * (p.mode == OUT_ROWPAIR ? 2 : 1);
-    const int64_t Nr = p.e.n * (p.mode == OUT_COLPAIR ? 2 : 1);
-    const int tm = static_cast<int>((Mr + T - 1) / T), tn = static_cast<int>((Nr + T - 1) / T);
-    for (int x = 0; x < tm; ++x)
-      for (int y = 0; y < tn; ++y) v.push_back({p.Kp, GroupTile{static_cast<int>(i), x, y}});
-  }
-  std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-  std::vector<GroupTile> out;
-  out.reserve(v.size());
-  for (auto& e : v) out.push_back(e.second);
-  return out;
-}
+std::vector<GroupTile> make_tiles(const Bucket& b, int variant) { return group_tiles(b.probs, variant); }
 
 }  // namespace
 
@@ -340,23 +369,8 @@ int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int metho
     b.tile_start.assign(1, 0);
     for (size_t j = 0; j < b.members.size(); ++j) {
       const Plan& P = g->plans[b.members[j]];
-      const Call& w = P.work;
-      char* pa = base + pack_off[b.members[j]];
-      char* pb = pa + P.bytes_a;
-      b.probs[j].A = pa;
-      b.probs[j].B = pb;
-      PackArgs ta{};
-      ta.src = w.A; ta.src_dt = w.dtA;
-      if (w.transa == MXG_TRANS || w.transa == MXG_CONJTRANS) { ta.smn = w.csA; ta.sk = w.rsA; }
-      else { ta.smn = w.rsA; ta.sk = w.csA; }
-      ta.MN = w.m; ta.K = w.k; ta.pattern = P.pat_a; ta.conj = P.conj_a;
-      ta.dst = pa; ta.ld = P.Mp; ta.MNp = P.Mp; ta.Kp = P.Kp; ta.layout = LAYOUT_MN_MAJOR; ta.split = SPLIT_NONE;
-      PackArgs tb{};
-      tb.src = w.B; tb.src_dt = w.dtB;
-      if (w.transb == MXG_TRANS || w.transb == MXG_CONJTRANS) { tb.smn = w.rsB; tb.sk = w.csB; }
-      else { tb.smn = w.csB; tb.sk = w.rsB; }
-      tb.MN = w.n; tb.K = w.k; tb.pattern = P.pat_b; tb.conj = P.conj_b;
-      tb.dst = pb; tb.ld = P.Np; tb.MNp = P.Np; tb.Kp = P.Kp; tb.layout = LAYOUT_MN_MAJOR; tb.split = SPLIT_NONE;
+      PackArgs ta{}, tb{};
+      group_describe_problem(P, base + pack_off[b.members[j]], &b.probs[j], &ta, &tb);
       for (const PackArgs& t : {ta, tb}) {
         b.tasks.push_back(t);
         b.tile_start.push_back(b.tile_start.back() + pack_tiles(t));

@@ -1,6 +1,8 @@
 // Device work lists and launchers of the grouped persistent launch.
 #pragma once
 
+#include <vector>
+
 #include "mxg_internal.h"
 
 namespace mxg {
@@ -49,6 +51,14 @@ __device__ __forceinline__ int next_tile(int* counter, int* slot, int prev, int 
 #endif
 
 int variant_tile(int variant);
+
+struct Plan;
+// The grouped-launch description of one planned problem (PLAN_GEMM on the SIMT / DMMA
+// layout) whose packed operands start at pa (A' then B'): its GroupProb and its two
+// pack tasks.
+void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta, PackArgs* tb);
+// Work list of (problem, tile) for a variant, ordered longest-K' first.
+std::vector<GroupTile> group_tiles(const std::vector<GroupProb>& probs, int variant);
 cudaError_t launch_dmma(int mode, int cdt, const GemmArgs& g, cudaStream_t s, dim3 grid);
 cudaError_t launch_dmma_grouped(const GroupProb* probs, const GroupTile* tiles, int ntiles, int* counter, int sched,
                                 int grid, cudaStream_t s);

@@ -116,3 +116,33 @@ def test_serving_configuration_sampled_blocks():
         ref = oracle_mxgemm("n", "n", al, Ab, Bb, be, np.array(C0, order="F"), comp=combo[3])
         err, _ = normwise_error(combo, got, ref, Ab, Bb, C0, al, be)
         assert err <= tolerance(combo, k), (combo, k, err)
+
+
+def test_small_requests_batched_into_waves_equal_solo():
+    """A burst of small requests (all combinations, transposes, both computation
+    precisions): those admitted while a wave runs on the high-priority stream are
+    batched into the next wave (one grouped launch); every result still equals the same
+    request run alone bit for bit and is within the bound of the oracle."""
+    import paper_1901_06015_gb300 as mx
+    probs = _problems(13, 240, lo=4, hi=64)
+    dev = [(to_device(p["A"]), to_device(p["B"]), to_device(p["C"])) for p in probs]
+    torch.cuda.synchronize()
+    srv = mx.Server(n_streams=3, hbm_budget_bytes=1 << 30, small_flops=1e7)
+    for p, (dA, dB, dC) in zip(probs, dev):
+        srv.submit((p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, p["combo"][3]))
+    srv.drain(120)
+    comps = srv.poll(1000)
+    st = srv.stats()
+    derr = srv.check_device_error()
+    srv.close()
+    assert derr == 0 and all(c["status"] == 0 for c in comps) and len(comps) == len(probs)
+    assert st["waves"] >= 1 and st["wave_requests"] >= 2 * st["waves"]
+    torch.cuda.synchronize()
+    for p, (_, _, dC) in zip(probs, dev):
+        got = dC.cpu().numpy()
+        assert np.array_equal(got, _solo(p, "ffma", "dfma")), p["combo"]
+        ref = oracle_mxgemm(p["ta"], p["tb"], p["alpha"], p["A"], p["B"], p["beta"], np.array(p["C"], order="K"),
+                            comp=p["combo"][3])
+        k = p["A"].shape[0] if p["ta"] in "th" else p["A"].shape[1]
+        err, _ = normwise_error(p["combo"], got, ref, p["A"], p["B"], p["C"], p["alpha"], p["beta"], p["ta"], p["tb"])
+        assert err <= tolerance(p["combo"], k), (p["combo"], err)
