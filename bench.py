@@ -434,7 +434,7 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                "overlap": "inputs copied on a side stream into three rotating device buffer sets (up to "
                           "two gemms ahead) while the current gemm computes; results read back on a third stream"}
-        del sets
+        del sets, host, out
 
     cpu = adhoc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -448,6 +448,18 @@ def run_ours(args):
                  "kind": "the paper's Ad-hoc (copy-cast to one datatype + same-type torch.matmul on the CPU)",
                  "sample": f"the same 512x256 blocks of C (k={n}) as cpu_baseline; useful flops 2mnkR"}
 
+    # %peak per combo: each call's useful GFLOPS (packs + contraction, CUDA events around
+    # the call) against the pipe its contraction runs on
+    # (theoretical peaks, as the paper's percentages are: FP32 lanes x 2 x max clock, and
+    # the FP64 pipe's nominal rate)
+    pct_peak = {c: round(100.0 * gf / (1e3 * (ffma_peak if c[3] == "s" else NOMINAL_FP64_TFLOPS)), 2)
+                for c, gf in per_combo.items()}
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        del mats
+        torch.cuda.empty_cache()
+        forms = {"grouped": grouped_form(args), "serving": serving_form(args)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOPS", "n_gpus": world,
@@ -456,8 +468,17 @@ def run_ours(args):
             "dtype": "f64+f32", "data": "synthetic", "config": workload_config(args),
             "roofline": roofline, "roofline_single": secondary, "pack_share_of_step": pack_share,
             "cpu_baseline": cpu, "adhoc_cpu": adhoc, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-            "per_combo_gflops": per_combo,
+            "per_combo_gflops": per_combo, "per_combo_pct_peak": pct_peak,
+            "per_combo_peaks": {"single": {"tflops": ffma_peak, "source": secondary["peak_source"]},
+                                "double": {"tflops": NOMINAL_FP64_TFLOPS,
+                                           "source": "nominal FP64 rate of GB300 (theoretical peak)"}},
         }
+        if forms is not None:
+            g, sv = forms["grouped"], forms["serving"]
+            line["grouped"] = {k: v for k, v in g.items() if k not in ("group",)}
+            line["grouped"]["kernels"] = [(b["precision"], b["kernel"], b["schedule"])
+                                          for b in g["group"].get("buckets", [])]
+            line["serving"] = sv
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -572,8 +593,9 @@ def grouped_problems(count, seed, lo, hi, dev):
     return items, flops
 
 
-def run_grouped(args):
-    """One graph-captured grouped launch of 2048 problems vs 2048 separate plain calls."""
+def grouped_form(args):
+    """One graph-captured grouped launch of args.count problems (autotuned) vs the same
+    problems as separate plain calls. Returns the measurement as a dict."""
     import torch
     import paper_1901_06015_gb300 as mx
     dev = torch.device("cuda", 0)
@@ -602,34 +624,45 @@ def run_grouped(args):
         for (ta, tb, al, A, B, be, C, x) in items:
             mx.mxgemm_ex(h, "auto", ta, tb, al, A, B, be, C, comp=x)
 
+    steps, warmup = max(args.steps, 5), max(args.warmup, 3)
     sampler = ClockSampler(0)
     sampler.start()
-    ms_g = timed(g.run, args.steps, args.warmup)
-    ms_s = timed(separate, args.steps, args.warmup)
+    ms_g = timed(g.run, steps, warmup)
+    ms_s = timed(separate, steps, warmup)
     clocks = sampler.stop()
     # the same grouped run without the tuner (first candidate, dynamic schedule)
     g2 = mx.Group(items, tune=False, graph=True, stream=stream)
-    ms_g2 = timed(g2.run, args.steps, args.warmup)
-    line = {"metric": METRIC, "workload": "grouped", "value": args.count / (ms_g / 1e3), "unit": "problems/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g,
+    ms_g2 = timed(g2.run, steps, warmup)
+    g.close(); g2.close(); h.close()
+    del items
+    torch.cuda.empty_cache()
+    return {"problems": args.count, "steps": steps, "warmup": warmup, "ms": ms_g,
+            "problems_per_s": args.count / (ms_g / 1e3), "gflops": flops / (ms_g / 1e3) / 1e9,
+            "separate_ms": ms_s, "separate_problems_per_s": args.count / (ms_s / 1e3),
+            "separate_gflops": flops / (ms_s / 1e3) / 1e9, "speedup_vs_separate": ms_s / ms_g,
+            "untuned_grouped_ms": ms_g2, "useful_gflop_per_run": flops / 1e9, "create_s": create_s,
+            "group": desc, "clocks": clocks,
+            "workload": f"batching: {args.count} independent gemms, m,n,k = round(exp(U(ln16, ln1024))), "
+                        "combination uniform over the 128, U[-1,1], alpha=1.5, beta=-0.5, seed 0; one "
+                        "graph-captured grouped persistent launch (autotuned) vs separate plain calls on one stream"}
+
+
+def run_grouped(args):
+    """The batching form alone (one JSON line)."""
+    r = grouped_form(args)
+    line = {"metric": METRIC, "workload": "grouped", "value": r["problems_per_s"], "unit": "problems/s",
+            "n_gpus": 1, "steps": r["steps"], "warmup": r["warmup"], "ms_per_step": r["ms"],
             "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": f"batching: {args.count} independent gemms, m,n,k = round(exp(U(ln16, ln1024))), "
-                                   "combination uniform over the 128, U[-1,1], alpha=1.5, beta=-0.5, seed 0; "
-                                   "one graph-captured grouped persistent launch (autotuned) vs separate plain calls"},
-            "grouped_gflops": flops / (ms_g / 1e3) / 1e9, "separate_ms": ms_s,
-            "separate_problems_per_s": args.count / (ms_s / 1e3), "separate_gflops": flops / (ms_s / 1e3) / 1e9,
-            "speedup_vs_separate": ms_s / ms_g, "untuned_grouped_ms": ms_g2,
-            "useful_gflop_per_step": flops / 1e9, "create_s": create_s, "group": desc, "clocks": clocks}
+            "config": {"workload": r["workload"]}, **{k: v for k, v in r.items() if k not in ("workload",)}}
     print(json.dumps(line))
-    g.close(); g2.close()
     return 0
 
 
 # ------------------------------------------------------------------ serving workload
-def run_serving(args):
+def serving_form(args):
     """Poisson arrivals of mixed-datatype requests (m, n, k log-uniform in [32, 4096],
     combination uniform over the 128, alpha, beta ~ U[-2, 2]) served with continuous
-    batching vs the same trace as serial plain calls on one stream."""
+    batching vs the same trace as serial plain calls on one stream. Returns a dict."""
     import numpy as np
     import torch
     import paper_1901_06015_gb300 as mx
@@ -698,11 +731,14 @@ def run_serving(args):
         lat = np.array([c["done"] - c["arrival"] for c in comps if c["status"] == 0])
         t_first = min(c["arrival"] for c in comps); t_last = max(c["done"] for c in comps)
         fl = sum(r[6] for r in todo)
+        large_wait = [c["admit"] - c["arrival"] for c in comps if c["flops"] > args.small_flops]
         return {"requests_per_s": len(lat) / (t_last - t_first), "gflops": fl / (t_last - t_first) / 1e9,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p90_ms": float(np.percentile(lat, 90) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
                 "failed": int(st["failed"]), "max_in_flight": int(st["max_in_flight"]),
-                "peak_bytes_in_flight": int(st["peak_bytes_in_flight"]), "span_s": t_last - t_first}
+                "peak_bytes_in_flight": int(st["peak_bytes_in_flight"]), "span_s": t_last - t_first,
+                "waves": int(st["waves"]), "wave_requests": int(st["wave_requests"]),
+                "max_queue_ms_large": float(max(large_wait) * 1e3) if large_wait else None}
 
     sampler = ClockSampler(0)
     sampler.start()
@@ -718,18 +754,32 @@ def run_serving(args):
                "capacity_ratio": sat_served["requests_per_s"] / sat_serial["requests_per_s"],
                "served_failed": sat_served["failed"], "serial_failed": sat_serial["failed"]}
     clocks = sampler.stop()
-    line = {"metric": METRIC, "workload": "serving", "value": served["requests_per_s"], "unit": "requests/s",
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": f"serving: {N} requests, Poisson arrivals at {args.load} x offline capacity, "
-                                   "m,n,k log-uniform in [32,4096], combination uniform over the 128, "
-                                   "alpha,beta ~ U[-2,2]; continuous batching over "
-                                   f"{args.streams} streams (small <= {args.small_flops:g} flops on a high-priority "
-                                   f"stream), HBM budget {args.budget_gb} GiB, vs serial plain calls on one stream",
-                       "requests": N, "load": args.load},
-            "capacity_requests_per_s": capacity, "arrival_rate": lam, "mean_service_ms": mean_service * 1e3,
-            "mean_request_gflop": total_flops / N / 1e9, "served": served, "serial": serial,
+    del poolA, poolB, poolC
+    torch.cuda.empty_cache()
+    # the FP64 pipe bounds both forms: the double-precision requests' flops at the nominal
+    # FP64 rate, per request of the trace
+    fp64_s = sum(r[6] for r in reqs if r[0][3] == "d" or (r[0][3] == "c" and r[0][0] in "dz")) / (
+        NOMINAL_FP64_TFLOPS * 1e12)
+    return {"requests": N, "load": args.load, "arrival_rate": lam, "capacity_requests_per_s": capacity,
+            "fp64_bound_requests_per_s": N / fp64_s if fp64_s > 0 else None,
+            "mean_service_ms": mean_service * 1e3, "mean_request_gflop": total_flops / N / 1e9,
+            "served": served, "serial": serial,
             "p99_speedup_vs_serial": serial["p99_ms"] / served["p99_ms"],
-            "p50_speedup_vs_serial": serial["p50_ms"] / served["p50_ms"], "saturation": sat, "clocks": clocks}
+            "p50_speedup_vs_serial": serial["p50_ms"] / served["p50_ms"], "saturation": sat, "clocks": clocks,
+            "workload": f"serving: {N} requests, Poisson arrivals at {args.load} x offline capacity, "
+                        "m,n,k log-uniform in [32,4096], combination uniform over the 128, alpha,beta ~ U[-2,2]; "
+                        f"continuous batching over {args.streams} streams (small <= {args.small_flops:g} flops on "
+                        f"a high-priority stream), HBM budget {args.budget_gb} GiB, vs serial plain calls on one "
+                        "stream"}
+
+
+def run_serving(args):
+    """The serving form alone (one JSON line)."""
+    r = serving_form(args)
+    line = {"metric": METRIC, "workload": "serving", "value": r["served"]["requests_per_s"], "unit": "requests/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": r["workload"], "requests": r["requests"], "load": r["load"]},
+            **{k: v for k, v in r.items() if k not in ("workload",)}}
     print(json.dumps(line))
     return 0
 
@@ -805,6 +855,8 @@ def main():
     ap.add_argument("--double-method", default="dmma", choices=["dmma", "dfma"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the grouped and serving forms that follow plain_large")
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision", "grouped", "serving", "single"])
     ap.add_argument("--count", type=int, default=2048)
     ap.add_argument("--combo", default="dddd")
