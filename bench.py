@@ -814,9 +814,12 @@ def run_single(args):
     C = operand(combo[0], lc, mm, nn)
     h = mx.Handle(); h.set_stream(stream)
     h.set_split_k(args.split_k)
+    h.set_cta_pairs(args.cta_pairs)
     R = real_products(combo)
     times = []
     h.set_phase_timing(True)
+    sampler = ClockSampler(0)
+    sampler.start()
     for i in range(args.warmup + args.reps):
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -827,6 +830,7 @@ def run_single(args):
             h.phase_times()
         if i >= args.warmup:
             times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
     pack_ms, con_ms, nl = h.phase_times()
     fl = 2.0 * mm * nn * kk * R
     # C is read and written once in its storage type (beta = 1): with k = 0 the call is the
@@ -835,12 +839,12 @@ def run_single(args):
     c_bytes = 2.0 * mm * nn * C.element_size() * (2 if C.dim() == 3 else 1)
     c_ms = (con_ms / nl) if nl else min(times)
     line = {"workload": "single", "combo": combo, "method": args.method, "m_n_k": [mm, nn, kk], "reps": args.reps,
-            "split_k": args.split_k,
+            "split_k": args.split_k, "cta_pairs": args.cta_pairs,
             "layout": [la, lb, lc], "trans": [args.transa, args.transb],
             "best_ms": min(times), "gflops": fl / min(times) / 1e6,
             "contraction_ms_mean": con_ms / max(nl, 1), "pack_ms_mean": pack_ms / max(nl, 1),
             "contraction_tflops": fl / (con_ms / max(nl, 1)) / 1e9 if nl else None,
-            "c_bytes": c_bytes, "c_gbs": c_bytes / c_ms / 1e6 if c_ms > 0 else None}
+            "c_bytes": c_bytes, "c_gbs": c_bytes / c_ms / 1e6 if c_ms > 0 else None, "clocks": clocks}
     print(json.dumps(line))
     return 0
 
@@ -866,6 +870,7 @@ def main():
     ap.add_argument("--transb", default="n")
     ap.add_argument("--mnk", default="", help="m,n,k for --workload single (default: --size cubed)")
     ap.add_argument("--split-k", type=int, default=0)
+    ap.add_argument("--cta-pairs", type=int, default=0, help="tensor-core methods: 0 auto, 1 pairs, 2 single CTAs")
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--streams", type=int, default=4)

@@ -207,6 +207,15 @@ int mxg_set_literal_alpha(mxg_handle h, int on);
  * tensor-core methods and grouped launches do not split. */
 int mxg_set_split_k(mxg_handle h, int mode);
 
+/* CTA pairs for the tensor-core methods (TF32X3, BF16X3, TC16) on h: mode 0 automatic
+ * (= pairs), 1 pairs, 2 one CTA per tile. A pair is a cluster of two CTAs on two SMs
+ * computing a 256 x 256 tile with tcgen05 cta_group::2 MMAs; each CTA loads its own
+ * half of the tile's A and B rows (128-byte k rows), so the operands cost a third fewer
+ * bytes, and half the requests, from L2 per flop than single-CTA 128 x 256 tiles. The
+ * two kernels give the same results bit for bit (tested; same products, accumulated in
+ * the same order along k). */
+int mxg_set_cta_pairs(mxg_handle h, int mode);
+
 /* Stream for subsequent calls on h (a cudaStream_t; NULL = legacy default stream). */
 int mxg_set_stream(mxg_handle h, void* stream);
 

@@ -193,6 +193,8 @@ int make_plan(const Call& c, int method, Plan* p) {
     P.plane_b = align256(static_cast<size_t>(P.Kp) * P.Np * esz);
     P.bytes_a = planes * P.plane_a;
     P.bytes_b = planes * P.plane_b;
+    // CTA pairs by default: half the operand rows per CTA per flop, 128-byte k rows
+    P.pairs = (c.cta_pairs != 2);
   } else {
     const size_t esz = P.comp_double ? 8 : 4;
     P.bytes_a = align256(static_cast<size_t>(P.Kp) * P.Mp * esz);
@@ -279,8 +281,10 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
     const bool one = (P.method == MXG_METHOD_TC16);
     const void* planes[4] = {base, one ? base : base + P.plane_a, base + P.bytes_a,
                              one ? base + P.bytes_a : base + P.bytes_a + P.plane_b};
-    const cudaError_t e = launch_gemm_tc(P.method, P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp,
-                                         plan_epilogue(P), dev_err, s);
+    const cudaError_t e =
+        P.pairs ? launch_gemm_tc_pair(P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P), dev_err, s)
+                : launch_gemm_tc(P.method, P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P), dev_err,
+                                 s);
     return e == cudaErrorNotSupported ? MXG_ENOTSUP : cuda_status(e);
   }
   GemmArgs g;
@@ -424,6 +428,13 @@ int mxg_set_split_k(mxg_handle h, int mode) {
   return MXG_OK;
 }
 
+int mxg_set_cta_pairs(mxg_handle h, int mode) {
+  if (!h || mode < 0 || mode > 2) return MXG_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->cta_pairs = mode;
+  return MXG_OK;
+}
+
 int mxg_set_literal_alpha(mxg_handle h, int on) {
   if (!h) return MXG_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
@@ -529,6 +540,7 @@ int mxgemm_ex(mxg_handle h, int method, int transa, int transb, int64_t m, int64
   c.literal_alpha = h->literal_alpha ? 1 : 0;
   c.split_k = h->split_k;
   c.sm_count = h->sm_count;
+  c.cta_pairs = h->cta_pairs;
   Plan P;
   int st = make_plan(c, method, &P);
   if (st != MXG_OK) return st;

@@ -322,9 +322,9 @@ TileCfg tile_cfg(int method) {
     case MXG_METHOD_FFMA: return {128, 128, 16};
     case MXG_METHOD_DFMA: return {64, 64, 8};
     case MXG_METHOD_DMMA: return {64, 64, 16};
-    case MXG_METHOD_TF32X3: return {128, 256, 16};   // tcgen05 tile 128 x 256, 64-byte k rows
-    case MXG_METHOD_BF16X3: return {128, 256, 32};
-    case MXG_METHOD_TC16: return {128, 256, 32};
+    case MXG_METHOD_TF32X3: return {128, 256, 32};   // tcgen05 tiles, k padded to 128 bytes
+    case MXG_METHOD_BF16X3: return {128, 256, 64};
+    case MXG_METHOD_TC16: return {128, 256, 64};
   }
   return {128, 128, 8};
 }

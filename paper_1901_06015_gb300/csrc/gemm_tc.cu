@@ -22,9 +22,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
-#include "epilogue.cuh"
+#include "tc_common.cuh"
 
 namespace mxg {
 
@@ -35,10 +36,11 @@ struct TcArgs {
   int* err;             // device error word set on a wait timeout (may be null)
 };
 
+using namespace tc;
+
 namespace {
 
 constexpr int TC_BM = 128, TC_BN = 256, TC_GM = 16;
-constexpr uint32_t ROWB = 64;                              // bytes of K per tile row (64-byte swizzle)
 constexpr uint32_t TILE_A = TC_BM * ROWB;                  // 8 KB
 constexpr uint32_t TILE_B = TC_BN * ROWB;                  // 16 KB
 constexpr uint32_t RING_BYTES = 192 * 1024;                // shared-memory ring
@@ -57,80 +59,6 @@ template <int SPLIT> struct TcFmt {
   static constexpr int stages = static_cast<int>(RING_BYTES / stage_bytes);   // 4 split, 8 TC16
 };
 constexpr uint32_t NBARS_MAX = 2 * 8 + 2 + 2 + 1;          // full, empty, acc_full, acc_empty, drain
-constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on the phase of the given parity; false after kWaitNs or when another
-// role of the CTA has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 255) == 0) {
-      if (*abort_flag) return false;
-      if (gtimer() - t0 > kWaitNs) return false;
-    }
-  }
-}
-// Bounded wait that ignores the abort flag (used to drain the CTA's own work).
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try(bar, parity))
-    if (gtimer() - t0 > kWaitNs) return;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-// Shared-memory matrix descriptor of a K-major tile written by TMA with the 64-byte
-// swizzle: rows of 64 bytes, 8-row swizzle atoms 512 bytes apart (stride byte
-// offset), leading byte offset unused for this layout (encoded as 1), descriptor
-// version 1, layout type 4 (64-byte swizzle).
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr >> 4) & 0x3fff);
-  d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(512 >> 4) << 32;
-  d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(4) << 61;
-  return d;
-}
-// Instruction descriptor (kind::f16 / kind::tf32): D in FP32, A and B of the given
-// format code (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32), both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
 
 template <int SPLIT>
 __device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
@@ -152,19 +80,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Tile t of the grouped order -> (m tile, n tile): groups of TC_GM m-tiles, n fastest
 // within a group column.
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int* tm, int* tn) {
@@ -174,57 +89,6 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   const int gsz = min(TC_GM, tiles_m - gm0);
   *tm = gm0 + r % gsz;
   *tn = r / gsz;
-}
-
-// Epilogue of one 32-column chunk of the accumulator (C datatype and mode fixed), in
-// two phases: tc_epi_load reads the thread's old C values for the chunk (all loads in
-// flight together, overlapping the TMEM read), tc_epi_finish updates and stores them.
-// ROWPAIR: rows 2i and 2i+1 (real and imaginary parts) sit in lanes 2l and 2l+1; the
-// even lane updates the even columns of the chunk, the odd lane the odd ones. COLPAIR: columns 2j, 2j+1 form one
-// complex column.
-template <int MODE> struct TcChunk { static constexpr int nold = (MODE == OUT_ROWPAIR || MODE == OUT_COLPAIR) ? 16 : 32; };
-
-template <int CDT, int MODE>
-__device__ __forceinline__ void tc_epi_load(const EpiArgs& e, int64_t row, int64_t col0, int lane,
-                                            COld<CDT> (&old)[TcChunk<MODE>::nold]) {
-  if constexpr (MODE == OUT_ROWPAIR) {
-#pragma unroll
-    for (int t = 0; t < 16; ++t) old[t] = epi_load<CDT>(e, row >> 1, col0 + 2 * t + (lane & 1));
-  } else if constexpr (MODE == OUT_COLPAIR) {
-#pragma unroll
-    for (int t = 0; t < 16; ++t) old[t] = epi_load<CDT>(e, row, (col0 >> 1) + t);
-  } else {
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) old[jj] = epi_load<CDT>(e, row, col0 + jj);
-  }
-}
-
-template <int CDT, int MODE>
-__device__ __forceinline__ void tc_epi_finish(const EpiArgs& e, const EpiScalars<float, CDT>& sc, int64_t row,
-                                              int64_t col0, const uint32_t (&v)[32], int lane,
-                                              const COld<CDT> (&old)[TcChunk<MODE>::nold]) {
-  if constexpr (MODE == OUT_ROWPAIR) {
-    // per column pair (2t, 2t+1) one exchange: the even lane sends its value of column
-    // 2t+1 and receives the odd lane's value of column 2t, so both lanes of the pair
-    // update one element (no divergence)
-    const bool odd = (lane & 1) != 0;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const float ve = __uint_as_float(v[2 * t]), vo = __uint_as_float(v[2 * t + 1]);
-      const float got = __shfl_xor_sync(0xffffffffu, odd ? ve : vo, 1);
-      const float pr = odd ? got : ve, pi = odd ? vo : got;
-      epi_update<float, CDT, MODE>(e, sc, row >> 1, col0 + 2 * t + (odd ? 1 : 0), pr, pi, old[t]);
-    }
-  } else if constexpr (MODE == OUT_COLPAIR) {
-#pragma unroll
-    for (int t = 0; t < 16; ++t)
-      epi_update<float, CDT, MODE>(e, sc, row, (col0 >> 1) + t, __uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]),
-                                   old[t]);
-  } else {
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj)
-      epi_update<float, CDT, MODE>(e, sc, row, col0 + jj, __uint_as_float(v[jj]), 0.0f, old[jj]);
-  }
 }
 
 template <int SPLIT>
@@ -411,7 +275,26 @@ __global__ void wait_timeout_probe(int* err, unsigned long long limit_ns) {
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
-int g_num_sms = 0;
+// SM count per device, filled on first use with that device current (several host
+// threads may race to fill an entry; they store the same value)
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_sms[kMaxDevices];
+
+cudaError_t current_sm_count(int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int v = g_sms[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (v <= 0) return cudaErrorInvalidValue;
+    g_sms[dev].store(v, std::memory_order_relaxed);
+  }
+  *out = v;
+  return cudaSuccess;
+}
 
 bool get_encoder() {
   std::call_once(g_encode_once, [] {
@@ -428,33 +311,42 @@ bool get_encoder() {
 
 // 2-D map over a K-major plane (rows x Kp elements, row pitch Kp elements), box
 // (rows_box x 64 bytes), 64-byte swizzle.
-bool make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box) {
+bool make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box,
+              uint32_t rowb = ROWB) {
   const int elem = (split == SPLIT_TF32) ? 4 : 2;
   const CUtensorMapDataType dtype = (split == SPLIT_TF32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                     : (split == SPLIT_F16_ONE) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(rows)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * elem};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(ROWB / elem), rows_box};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(rowb / elem), rows_box};
   const cuuint32_t estr[2] = {1u, 1u};
   const CUresult r = g_encode(map, dtype, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 template <int SPLIT>
-cudaError_t launch_one(const CUtensorMap* maps, const TcArgs& g, cudaStream_t s) {
+cudaError_t launch_one(const CUtensorMap* maps, const TcArgs& g, int sms, cudaStream_t s) {
   auto kern = tc_split_gemm<SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (g.Mp / TC_BM) * (g.Np / TC_BN);
-  const int grid = static_cast<int>(ntiles < g_num_sms ? ntiles : g_num_sms);
+  const int grid = static_cast<int>(ntiles < sms ? ntiles : sms);
   kern<<<grid, 192, TC_SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], g);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+bool tc_get_encoder() { return get_encoder(); }
+bool tc_make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box,
+                 uint32_t rowb) {
+  return make_map(map, ptr, split, rows, Kp, rows_box, rowb);
+}
+cudaError_t tc_current_sm_count(int* out) { return current_sm_count(out); }
 
 cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s) {
   wait_timeout_probe<<<1, 32, 0, s>>>(err, static_cast<unsigned long long>(seconds * 1e9));
@@ -470,12 +362,9 @@ cudaError_t launch_gemm_tc(int method, int split, int c_dt, int mode, const void
   if (Mp % TC_BM || Np % TC_BN || Kp % bk) return cudaErrorInvalidValue;
   if ((Mp / TC_BM) * (Np / TC_BN) > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (Mp == 0 || Np == 0) return cudaSuccess;
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaError_t ce = cudaGetDevice(&dev);
-    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (ce != cudaSuccess || g_num_sms <= 0) return ce != cudaSuccess ? ce : cudaErrorInvalidValue;
-  }
+  int sms = 0;
+  const cudaError_t ce = current_sm_count(&sms);
+  if (ce != cudaSuccess) return ce;
   CUtensorMap maps[4];
   if (!make_map(&maps[0], planes[0], split, Mp, Kp, TC_BM) || !make_map(&maps[1], planes[1], split, Mp, Kp, TC_BM) ||
       !make_map(&maps[2], planes[2], split, Np, Kp, TC_BN) || !make_map(&maps[3], planes[3], split, Np, Kp, TC_BN))
@@ -485,10 +374,10 @@ cudaError_t launch_gemm_tc(int method, int split, int c_dt, int mode, const void
   with_c_mode(c_dt, mode, [&](auto, auto) { valid = true; });
   if (!valid) return cudaErrorInvalidValue;
   switch (split) {
-    case SPLIT_TF32: return launch_one<SPLIT_TF32>(maps, g, s);
-    case SPLIT_BF16: return launch_one<SPLIT_BF16>(maps, g, s);
-    case SPLIT_F16_ONE: return launch_one<SPLIT_F16_ONE>(maps, g, s);
-    case SPLIT_BF16_ONE: return launch_one<SPLIT_BF16_ONE>(maps, g, s);
+    case SPLIT_TF32: return launch_one<SPLIT_TF32>(maps, g, sms, s);
+    case SPLIT_BF16: return launch_one<SPLIT_BF16>(maps, g, sms, s);
+    case SPLIT_F16_ONE: return launch_one<SPLIT_F16_ONE>(maps, g, sms, s);
+    case SPLIT_BF16_ONE: return launch_one<SPLIT_BF16_ONE>(maps, g, sms, s);
   }
   return cudaErrorInvalidValue;
 }

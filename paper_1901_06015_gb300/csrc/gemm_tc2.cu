@@ -1,0 +1,410 @@
+// Tensor-core contraction on CTA pairs (tcgen05 cta_group::2, sm_103a).
+//
+// The same product as tc_split_gemm (one pass for the binary16 / bfloat16 computation
+// precisions, hi*hi + hi*lo + lo*hi for the split forms, FP32 accumulation over the
+// whole K' in tensor memory, the fused epilogue of Sec. 7.1), computed on 256 x 256
+// tiles of P by a cluster of two CTAs on two SMs. Each CTA loads its own 128 rows of A
+// and its own 128 rows of B (plain per-CTA TMA loads, no multicast); one MMA of
+// M = 256, N = 256 issued by the even CTA of the pair reads A from both CTAs' shared
+// memory (one half each) and B from both (one half each), and writes each CTA's 128
+// rows of the accumulator into that CTA's tensor memory. Per k-block a CTA therefore
+// moves 128 + 128 rows of operands for a 128 x 256 share of the tile, against 128 +
+// 256 rows in the one-CTA kernel: a third fewer bytes from L2 per flop, in half as many
+// row requests (128-byte rows), which is what bounds the one-pass 16-bit form there.
+//
+// Roles (192 threads per CTA, one CTA per SM, persistent over pair tiles):
+//   warp 0      TMA producer in both CTAs: its halves of A and B, in 128-byte k rows
+//               with the 128-byte swizzle, into its own 6- (split forms: 3-) stage
+//               ring; the completion of both CTAs' copies is counted on the even CTA's
+//               "full" barrier (.cta_group::2 copies);
+//   warp 1      both CTAs allocate the two 128 x 256 FP32 accumulators together
+//               (cta_group::2); in the even CTA one lane issues the MMAs, frees each
+//               stage in both CTAs and hands a finished accumulator to both CTAs'
+//               epilogues (one tcgen05.commit per CTA, no multicast);
+//   warps 2..5  epilogue in both CTAs over the CTA's own 128 rows, then an arrival on
+//               the even CTA's accumulator-empty barrier (eight arrivals per use).
+// Every wait is bounded in time; on expiry a CTA sets the error word and both CTAs'
+// abort flags, skips its stores, drains its own MMAs and copies (bounded), and the pair
+// meets at a final cluster barrier before freeing tensor memory, so neither CTA exits
+// while the other may still touch its shared or tensor memory.
+#include <algorithm>
+
+#include "tc_common.cuh"
+
+namespace mxg {
+
+using namespace tc;
+
+namespace {
+
+constexpr int P_BM = 128;                         // rows of A per CTA (256 per pair)
+constexpr int P_BN = 256;                         // columns of the pair tile (MMA N)
+constexpr int P_GM = 8;                           // pair rows per group of the tile order
+// Bytes of K per tile row, with the swizzle of that width. 128-byte rows halve the
+// number of row requests TMA sends to L2 per byte against 64-byte rows; with 64-byte
+// rows the request path, not the bytes, limited the one-pass 16-bit form (measured on
+// GB300 at 8192^3: 1.25 PF/s with 64-byte rows, 1.66 PF/s with 128-byte rows).
+constexpr int P_RB = 128;
+constexpr uint32_t P_RING = 192 * 1024;
+constexpr uint32_t P_SMEM = P_RING + 1024 + 512;
+constexpr uint32_t P_TMEM_COLS = 2 * P_BN;        // two accumulators
+
+// RB: bytes of K per tile row (64 or 128, with the swizzle of that width).
+template <int SPLIT, int RB> struct PairFmt {
+  static constexpr int planes = (SPLIT == SPLIT_F16_ONE || SPLIT == SPLIT_BF16_ONE) ? 1 : 2;
+  static constexpr int elem = (SPLIT == SPLIT_TF32) ? 4 : 2;
+  static constexpr uint32_t fmt = (SPLIT == SPLIT_TF32) ? 2u : (SPLIT == SPLIT_F16_ONE ? 0u : 1u);
+  static constexpr uint32_t tile_a = P_BM * RB;          // this CTA's rows of A
+  static constexpr uint32_t tile_b = (P_BN / 2) * RB;    // this CTA's half of B
+  static constexpr uint32_t stage_bytes = planes * (tile_a + tile_b);
+  // 128-byte rows: 6 stages one-pass, 3 split (64-byte rows: 12 and 6)
+  static constexpr int stages = static_cast<int>(P_RING / stage_bytes);
+};
+constexpr int P_NBARS = 2 * 12 + 2 + 2 + 1;       // full, empty, acc_full, acc_empty, drain
+
+struct PairArgs {
+  int64_t Mp, Np, Kp;
+  EpiArgs e;
+  int cdt, mode;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t cta_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory object in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+// Wait with cluster-scope acquire (barriers completed by the other CTA of the pair).
+__device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_cl(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_cl(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kWaitNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void mbar_drain_cl(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_cl(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return;
+}
+// TMA tile load into this CTA's shared memory whose completion is counted on `bar`,
+// which may be the barrier of either CTA of the pair (shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                                 uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+template <int SPLIT>
+__device__ __forceinline__ void mma_pair(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  constexpr uint32_t idesc = make_idesc(PairFmt<SPLIT, 64>::fmt, 2 * P_BM, P_BN);
+  if constexpr (SPLIT != SPLIT_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  }
+}
+// Arrive on `cluster_bar` (either CTA's barrier) once every MMA this thread issued so
+// far has completed.
+__device__ __forceinline__ void commit_pair(uint32_t cluster_bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cluster_bar)
+               : "memory");
+}
+
+// Pair tile t of the grouped order -> (pair row, column tile).
+__device__ __forceinline__ void pair_coords(int t, int pairs_m, int tiles_n, int* pm, int* tn) {
+  const int per_group = P_GM * tiles_n;
+  const int g = t / per_group, r = t - g * per_group;
+  const int gm0 = g * P_GM;
+  const int gsz = min(P_GM, pairs_m - gm0);
+  *pm = gm0 + r % gsz;
+  *tn = r / gsz;
+}
+
+template <int SPLIT, int RB>
+__global__ void __launch_bounds__(192, 1)
+tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+             const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, PairArgs g) {
+  using F = PairFmt<SPLIT, RB>;
+  constexpr int S = F::stages;
+  constexpr uint32_t STAGE_BYTES = F::stage_bytes;
+  constexpr uint32_t P_TILE_A = F::tile_a, P_TILE_B = F::tile_b;
+  constexpr int BK = RB / F::elem;          // k elements per row
+  constexpr int KSTEPS = RB / 32;           // MMAs per row (each consumes 32 bytes of K)
+  static_assert(2 * S + 5 <= P_NBARS, "barrier area");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gen_base = smem_raw + (base - raw);
+  const uint32_t bars = base + S * STAGE_BYTES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + S * STAGE_BYTES + 8 * P_NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (S + s); };
+  auto acc_full = [&](int b) { return bars + 8u * (2 * S + b); };
+  auto acc_empty = [&](int b) { return bars + 8u * (2 * S + 2 + b); };
+  const uint32_t drain_bar = bars + 8u * (2 * S + 4);
+
+  const uint32_t rank = cta_rank();               // 0: issues the MMAs; 1: its peer
+  const bool leader = (rank == 0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pairs_m = static_cast<int>((g.Mp + 2 * P_BM - 1) / (2 * P_BM));
+  const int tiles_n = static_cast<int>(g.Np / P_BN);
+  const int ntiles = pairs_m * tiles_n;
+  const int nkb = static_cast<int>(g.Kp / BK);
+  const int cid = static_cast<int>(blockIdx.x >> 1), ncl = static_cast<int>(gridDim.x >> 1);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 1);      // the even CTA's arrive.expect_tx, plus both CTAs' bytes
+      mbar_init(empty(s), 1);     // one commit of the even CTA's MMAs
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 8);   // four epilogue warps in each CTA of the pair
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {   // both CTAs allocate together: the same columns in each
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(P_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();   // both CTAs' barriers exist before either touches the other's
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t peer = rank ^ 1u;
+  auto fail = [&]() {
+    if (g.err) atomicExch(g.err, 1);
+    *abort_flag = 1;
+    st_cluster_u32(peer_addr(smem_u32(const_cast<int*>(abort_flag)), peer), 1u);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = cid; t < ntiles && ok; t += ncl) {
+        int pm, tn;
+        pair_coords(t, pairs_m, tiles_n, &pm, &tn);
+        const int32_t ym = pm * 2 * P_BM + static_cast<int32_t>(rank) * P_BM;
+        const int32_t yn = tn * P_BN + static_cast<int32_t>(rank) * (P_BN / 2);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = static_cast<int>(it % S);
+          const uint32_t use = it / S;
+          if (!mbar_wait_cl(empty(s), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          const uint32_t st = base + s * STAGE_BYTES;
+          // both CTAs' copies complete on the even CTA's full barrier; only the even CTA
+          // arrives on it, announcing both halves' bytes
+          const uint32_t fb = leader ? full(s) : peer_addr(full(s), 0);
+          if (leader) mbar_expect_tx(full(s), 2 * STAGE_BYTES);
+          const int32_t kx = kb * BK;
+          tma_load_2d_pair(st, &mAh, kx, ym, fb);
+          if constexpr (F::planes == 2) tma_load_2d_pair(st + P_TILE_A, &mAl, kx, ym, fb);
+          tma_load_2d_pair(st + F::planes * P_TILE_A, &mBh, kx, yn, fb);
+          if constexpr (F::planes == 2) tma_load_2d_pair(st + 2 * P_TILE_A + P_TILE_B, &mBl, kx, yn, fb);
+        }
+      }
+      if (!ok) {
+        fail();
+        // the even CTA waits (bounded) for the copies it counted: the last use of every stage
+        if (leader)
+          for (uint32_t j = (it > static_cast<uint32_t>(S) ? it - S : 0); j < it; ++j)
+            mbar_drain_cl(full(j % S), (j / S) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      uint32_t it = 0;
+      bool ok = true;
+      int j = 0;
+      for (int t = cid; t < ntiles && ok; t += ncl, ++j) {
+        const int b = j & 1;
+        if (!mbar_wait_cl(acc_empty(b), (static_cast<uint32_t>(j >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_tmem = tmem + static_cast<uint32_t>(b * P_BN);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = static_cast<int>(it % S);
+          if (!mbar_wait_cl(full(s), (it / S) & 1u, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint32_t a_hi = st, a_lo = st + P_TILE_A, b_hi = st + F::planes * P_TILE_A, b_lo = b_hi + P_TILE_B;
+#pragma unroll
+          for (int kk = 0; kk < KSTEPS; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_pair<SPLIT>(acc_tmem, swz_desc<RB>(a_hi + off), swz_desc<RB>(b_hi + off), first);
+            if constexpr (F::planes == 2) {
+              mma_pair<SPLIT>(acc_tmem, swz_desc<RB>(a_hi + off), swz_desc<RB>(b_lo + off), 1u);
+              mma_pair<SPLIT>(acc_tmem, swz_desc<RB>(a_lo + off), swz_desc<RB>(b_hi + off), 1u);
+            }
+          }
+          commit_pair(empty(s));                    // this CTA's stage is free ...
+          commit_pair(peer_addr(empty(s), peer));   // ... and the peer's
+        }
+        if (!ok) break;
+        commit_pair(acc_full(b));
+        commit_pair(peer_addr(acc_full(b), peer));
+      }
+      if (!ok) fail();
+      // every MMA this thread issued has completed once the drain barrier flips
+      commit_pair(drain_bar);
+      mbar_drain_cl(drain_bar, 0);
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter q = warp % 4 of this CTA's 128 rows
+    const int q = warp & 3;
+    int j = 0;
+    for (int t = cid; t < ntiles; t += ncl, ++j) {
+      int pm, tn;
+      pair_coords(t, pairs_m, tiles_n, &pm, &tn);
+      const int b = j & 1;
+      const bool ok = mbar_wait_cl(acc_full(b), static_cast<uint32_t>(j >> 1) & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, ok && !*abort_flag)) {
+        if (lane == 0 && !ok) fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t m0 = static_cast<int64_t>(pm) * 2 * P_BM + static_cast<int64_t>(rank) * P_BM;
+      const int64_t n0 = static_cast<int64_t>(tn) * P_BN;
+      const int64_t row = m0 + 32 * q + lane;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b * P_BN);
+      with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
+        constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
+        const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(g.e);
+#pragma unroll 1
+        for (int c0 = 0; c0 < P_BN; c0 += 32) {
+          COld<CDT> old[TcChunk<MODE>::nold];
+          tc_epi_load<CDT, MODE>(g.e, row, n0 + c0, lane, old);
+          uint32_t v[32];
+          tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
+          tc_epi_finish<CDT, MODE>(g.e, sc, row, n0 + c0, v, lane, old);
+        }
+      });
+      // release the accumulator to the even CTA's MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (leader) mbar_arrive(acc_empty(b));
+        else mbar_arrive_cluster(peer_addr(acc_empty(b), 0));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  __syncwarp();
+  cluster_sync_all();   // neither CTA leaves while the other may still use its memory
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P_TMEM_COLS) : "memory");
+  }
+}
+
+template <int SPLIT, int RB>
+cudaError_t launch_pair(const CUtensorMap* maps, const PairArgs& g, int sms, cudaStream_t s) {
+  auto kern = tc_pair_gemm<SPLIT, RB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM);
+  if (e != cudaSuccess) return e;
+  const int64_t npairs = ((g.Mp + 2 * P_BM - 1) / (2 * P_BM)) * (g.Np / P_BN);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = P_SMEM;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * (sms / 2)), 1, 1);
+  // persistent: as many pairs as can be resident at once (at most one CTA per SM)
+  int max_clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg) != cudaSuccess || max_clusters <= 0) {
+    cudaGetLastError();
+    max_clusters = sms / 2;
+  }
+  const int64_t ncl = std::min<int64_t>(npairs, std::min(max_clusters, sms / 2));
+  if (ncl <= 0) return cudaErrorInvalidValue;
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl), 1, 1);
+  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], g);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace
+
+// planes: A_hi, A_lo (Mp x Kp, K-major), B_hi, B_lo (Np x Kp, K-major); one plane per
+// operand for the one-pass formats (the lo entries are ignored)
+cudaError_t launch_gemm_tc_pair(int split, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,
+                                int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s) {
+  if (!tc_get_encoder()) return cudaErrorNotSupported;
+  const int elem = (split == SPLIT_TF32) ? 4 : 2;
+  if (Mp % P_BM || Np % P_BN || (Kp * elem) % P_RB) return cudaErrorInvalidValue;
+  if (Mp == 0 || Np == 0) return cudaSuccess;
+  if (((Mp + 2 * P_BM - 1) / (2 * P_BM)) * (Np / P_BN) > 0x7fffffffLL) return cudaErrorInvalidValue;
+  int sms = 0;
+  const cudaError_t ce = tc_current_sm_count(&sms);
+  if (ce != cudaSuccess) return ce;
+  if (sms < 2) return cudaErrorNotSupported;
+  CUtensorMap maps[4];
+  if (!tc_make_map(&maps[0], planes[0], split, Mp, Kp, P_BM, P_RB) ||
+      !tc_make_map(&maps[1], planes[1], split, Mp, Kp, P_BM, P_RB) ||
+      !tc_make_map(&maps[2], planes[2], split, Np, Kp, P_BN / 2, P_RB) ||
+      !tc_make_map(&maps[3], planes[3], split, Np, Kp, P_BN / 2, P_RB))
+    return cudaErrorInvalidValue;
+  PairArgs g{Mp, Np, Kp, e, c_dt, mode, err};
+  bool valid = false;
+  with_c_mode(c_dt, mode, [&](auto, auto) { valid = true; });
+  if (!valid) return cudaErrorInvalidValue;
+  switch (split) {
+    case SPLIT_TF32: return launch_pair<SPLIT_TF32, P_RB>(maps, g, sms, s);
+    case SPLIT_BF16: return launch_pair<SPLIT_BF16, P_RB>(maps, g, sms, s);
+    case SPLIT_F16_ONE: return launch_pair<SPLIT_F16_ONE, P_RB>(maps, g, sms, s);
+    case SPLIT_BF16_ONE: return launch_pair<SPLIT_BF16_ONE, P_RB>(maps, g, sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mxg

@@ -105,5 +105,9 @@ cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s);
 // operand for the TC16 formats: the lo entries are ignored).
 cudaError_t launch_gemm_tc(int method, int split, int c_dt, int mode, const void* const planes[4], int64_t Mp,
                            int64_t Np, int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s);
+// The same contraction on CTA pairs (tcgen05 cta_group::2, 256 x 256 pair tiles; Mp a
+// multiple of 128, Np of 256).
+cudaError_t launch_gemm_tc_pair(int split, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,
+                                int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s);
 
 }  // namespace mxg

@@ -19,6 +19,7 @@ struct Call {
   int literal_alpha;   // Sec. 7.2's literal reading: complex alpha honoured in every case
   int split_k;         // 0 off, 1 automatic, >= 2 that many K slices (SIMT and DMMA methods)
   int sm_count;        // SMs of the device (0: assume 152) for the automatic split
+  int cta_pairs;       // tensor-core methods: 0 automatic, 1 CTA pairs, 2 single CTAs
 };
 
 enum PlanKind : int { PLAN_NOOP = 0, PLAN_SCALE = 1, PLAN_GEMM = 2 };
@@ -41,6 +42,7 @@ struct Plan {
   int64_t Mr = 0, Nr = 0, Kr = 0;   // real gemm
   int64_t Mp = 0, Np = 0, Kp = 0;   // padded to the kernel's tiles
   int split = SPLIT_NONE;           // hi/lo planes for the tensor-core methods
+  bool pairs = false;               // tensor-core contraction on CTA pairs
   size_t plane_a = 0, plane_b = 0;  // bytes of one plane (split methods)
   int splits = 1;                   // split-K slices
   int64_t kslice = 0;               // k elements per slice

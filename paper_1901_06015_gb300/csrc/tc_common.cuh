@@ -1,0 +1,179 @@
+// Device helpers shared by the tcgen05 contraction kernels (sm_103a): bounded mbarrier
+// waits, TMA tile loads, shared-memory and instruction descriptors, TMEM loads, and the
+// 32-column epilogue chunk that pairs rows or columns for complex C. Host helpers: the
+// tensor-map encoder, 2-D K-major tensor maps, and the SM count of the current device.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "epilogue.cuh"
+
+namespace mxg {
+namespace tc {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
+constexpr uint32_t ROWB = 64;                              // bytes of K per tile row (64-byte swizzle)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on the phase of the given parity; false after kWaitNs or when another
+// role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kWaitNs) return false;
+    }
+  }
+}
+// Bounded wait that ignores the abort flag (used to drain the CTA's own work).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the 64-byte
+// swizzle: rows of 64 bytes, 8-row swizzle atoms 512 bytes apart (stride byte
+// offset), leading byte offset unused for this layout (encoded as 1), descriptor
+// version 1, layout type 4 (64-byte swizzle).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3fff);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;
+  return d;
+}
+// The same for rows of RB bytes (64 or 128) written with the RB-byte swizzle: 8-row
+// atoms of 8 * RB bytes, layout type 4 (64-byte) or 2 (128-byte).
+template <uint32_t RB>
+__device__ __forceinline__ uint64_t swz_desc(uint32_t saddr) {
+  static_assert(RB == 64 || RB == 128, "swizzle width");
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3fff);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>((8 * RB) >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(RB == 128 ? 2 : 4) << 61;
+  return d;
+}
+// Instruction descriptor (kind::f16 / kind::tf32): D in FP32, A and B of the given
+// format code (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Epilogue of one 32-column chunk of the accumulator (C datatype and mode fixed), in
+// two phases: tc_epi_load reads the thread's old C values for the chunk (all loads in
+// flight together, overlapping the TMEM read), tc_epi_finish updates and stores them.
+// ROWPAIR: rows 2i and 2i+1 (real and imaginary parts) sit in lanes 2l and 2l+1; the
+// even lane updates the even columns of the chunk, the odd lane the odd ones. COLPAIR: columns 2j, 2j+1 form one
+// complex column.
+template <int MODE> struct TcChunk { static constexpr int nold = (MODE == OUT_ROWPAIR || MODE == OUT_COLPAIR) ? 16 : 32; };
+
+template <int CDT, int MODE>
+__device__ __forceinline__ void tc_epi_load(const EpiArgs& e, int64_t row, int64_t col0, int lane,
+                                            COld<CDT> (&old)[TcChunk<MODE>::nold]) {
+  if constexpr (MODE == OUT_ROWPAIR) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) old[t] = epi_load<CDT>(e, row >> 1, col0 + 2 * t + (lane & 1));
+  } else if constexpr (MODE == OUT_COLPAIR) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) old[t] = epi_load<CDT>(e, row, (col0 >> 1) + t);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) old[jj] = epi_load<CDT>(e, row, col0 + jj);
+  }
+}
+
+template <int CDT, int MODE>
+__device__ __forceinline__ void tc_epi_finish(const EpiArgs& e, const EpiScalars<float, CDT>& sc, int64_t row,
+                                              int64_t col0, const uint32_t (&v)[32], int lane,
+                                              const COld<CDT> (&old)[TcChunk<MODE>::nold]) {
+  if constexpr (MODE == OUT_ROWPAIR) {
+    // per column pair (2t, 2t+1) one exchange: the even lane sends its value of column
+    // 2t+1 and receives the odd lane's value of column 2t, so both lanes of the pair
+    // update one element (no divergence)
+    const bool odd = (lane & 1) != 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const float ve = __uint_as_float(v[2 * t]), vo = __uint_as_float(v[2 * t + 1]);
+      const float got = __shfl_xor_sync(0xffffffffu, odd ? ve : vo, 1);
+      const float pr = odd ? got : ve, pi = odd ? vo : got;
+      epi_update<float, CDT, MODE>(e, sc, row >> 1, col0 + 2 * t + (odd ? 1 : 0), pr, pi, old[t]);
+    }
+  } else if constexpr (MODE == OUT_COLPAIR) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      epi_update<float, CDT, MODE>(e, sc, row, (col0 >> 1) + t, __uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]),
+                                   old[t]);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj)
+      epi_update<float, CDT, MODE>(e, sc, row, col0 + jj, __uint_as_float(v[jj]), 0.0f, old[jj]);
+  }
+}
+
+}  // namespace tc
+
+// Host side (defined in gemm_tc.cu).
+bool tc_get_encoder();
+// 2-D map over a K-major plane (rows x Kp elements, row pitch Kp elements), box
+// (rows_box x rowb bytes), rowb-byte swizzle (rowb = 64 or 128); rows past the plane
+// read as zero.
+bool tc_make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box,
+                 uint32_t rowb);
+cudaError_t tc_current_sm_count(int* out);
+
+}  // namespace mxg

@@ -85,6 +85,8 @@ def lib():
             L.mxg_destroy.argtypes = [_vp]
             L.mxg_set_split_k.restype = _i32
             L.mxg_set_split_k.argtypes = [_vp, _i32]
+            L.mxg_set_cta_pairs.restype = _i32
+            L.mxg_set_cta_pairs.argtypes = [_vp, _i32]
             L.mxg_set_literal_alpha.restype = _i32
             L.mxg_set_literal_alpha.argtypes = [_vp, _i32]
             L.mxg_set_stream.restype = _i32
@@ -217,6 +219,12 @@ class Handle:
         st = lib().mxg_set_split_k(self.h, int(mode))
         if st:
             raise MxgError(st, "mxg_set_split_k")
+
+    def set_cta_pairs(self, mode):
+        """Tensor-core methods on CTA pairs: 0 automatic, 1 always, 2 never."""
+        st = lib().mxg_set_cta_pairs(self.h, int(mode))
+        if st:
+            raise MxgError(st, "mxg_set_cta_pairs")
 
     def set_literal_alpha(self, on):
         """Sec. 7.2's literal reading of a complex alpha for calls on this handle."""

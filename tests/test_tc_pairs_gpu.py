@@ -1,0 +1,58 @@
+"""Tensor-core contraction on CTA pairs (tcgen05 cta_group::2; GPU). The pair kernel
+(256 x 256 tiles over two SMs) and the single-CTA kernel (128 x 256 tiles) compute the
+same products in the same order along k, so their results agree bit for bit; both are
+within the stated bound of the oracle. Shapes cover an odd number of 128-row tiles
+(the last pair's second half lies past the packed operand), ragged edges, every output
+mode, the one-pass 16-bit form and the split forms."""
+import numpy as np
+import pytest
+
+from oracle import oracle_mxgemm
+from paper_1901_06015_gb300 import synth
+from tests._helpers import normwise_error, tolerance
+from tests.gpu_util import from_device, to_device
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # combo, (m, n, k), method
+    ("hhhh", (300, 260, 96), "tc16"),        # Mp = 384: three 128-row tiles, odd
+    ("bbbb", (128, 256, 32), "tc16"),        # one pair, half of it past Mp
+    ("kkkh", (140, 270, 96), "tc16"),        # case 3, row pairs
+    ("wbwb", (257, 513, 160), "tc16"),       # case 2bc, column pairs
+    ("zbbb", (90, 130, 200), "tc16"),        # case 1c, Re(C) only
+    ("shhh", (520, 700, 64), "tc16"),
+    ("ssss", (300, 260, 320), "bf16x3"),
+    ("zcds", (129, 300, 64), "tf32x3"),
+    ("cscs", (150, 260, 330), "bf16x3"),
+]
+
+
+def _run(h, combo, method, A, B, C0, alpha, beta):
+    import paper_1901_06015_gb300 as mx
+    dA, dB, dC = to_device(A), to_device(B), to_device(C0)
+    mx.mxgemm_ex(h, method, "n", "n", alpha, dA, dB, beta, dC, comp=combo[3])
+    torch.cuda.synchronize()
+    return from_device(dC, combo[0])
+
+
+@pytest.mark.parametrize("combo,shape,method", CASES)
+def test_pairs_equal_single_cta_and_oracle(combo, shape, method):
+    import paper_1901_06015_gb300 as mx
+    m, n, k = shape
+    A, B, C0 = synth.problem(41, combo, m, n, k)
+    alpha = (1.25 - 0.5j) if all(synth.is_complex(t) for t in combo[:3]) else 1.5
+    beta = (-0.5 + 0.25j) if synth.is_complex(combo[0]) else -0.5
+    hp, hs = mx.Handle(), mx.Handle()
+    for h, mode in ((hp, 1), (hs, 2)):
+        h.set_stream(torch.cuda.current_stream())
+        h.set_cta_pairs(mode)
+    got_p = _run(hp, combo, method, A, B, C0, alpha, beta)
+    got_s = _run(hs, combo, method, A, B, C0, alpha, beta)
+    assert hp.check_device_error() == 0 and hs.check_device_error() == 0
+    assert np.array_equal(synth.to_c128(got_p), synth.to_c128(got_s)), (combo, method)
+    ref = oracle_mxgemm("n", "n", alpha, A, B, beta, C0.copy(), comp=combo[3])
+    err, _ = normwise_error(combo, got_p, ref, A, B, C0, alpha, beta)
+    assert err <= tolerance(combo, k, method, beta), (combo, method, err)
+    hp.close(); hs.close()
