@@ -603,7 +603,7 @@ def grouped_form(args):
     items, flops = grouped_problems(args.count, 0, 16, 1024, dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = mx.Group(items, tune=True, graph=True, stream=stream)
+    g = mx.Group(items, tune=True, graph=True, stream=stream, method_s=args.method_s)
     create_s = time.perf_counter() - t0
     desc = g.describe()
     h = mx.Handle(); h.set_stream(stream)
@@ -620,9 +620,13 @@ def grouped_form(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
+    k_of = [(A.shape[0] if ta in "th" else A.shape[1]) for (ta, tb, al, A, B, be, C, x) in items]
+    min_k = {"bf16x3": 320, "tf32x3": 32}.get(args.method_s, 0)
+
     def separate():
-        for (ta, tb, al, A, B, be, C, x) in items:
-            mx.mxgemm_ex(h, "auto", ta, tb, al, A, B, be, C, comp=x)
+        for (ta, tb, al, A, B, be, C, x), k in zip(items, k_of):
+            meth = args.method_s if (x == "s" and k >= min_k and args.method_s != "auto") else "auto"
+            mx.mxgemm_ex(h, meth, ta, tb, al, A, B, be, C, comp=x)
 
     steps, warmup = max(args.steps, 5), max(args.warmup, 3)
     sampler = ClockSampler(0)
@@ -631,7 +635,7 @@ def grouped_form(args):
     ms_s = timed(separate, steps, warmup)
     clocks = sampler.stop()
     # the same grouped run without the tuner (first candidate, dynamic schedule)
-    g2 = mx.Group(items, tune=False, graph=True, stream=stream)
+    g2 = mx.Group(items, tune=False, graph=True, stream=stream, method_s=args.method_s)
     ms_g2 = timed(g2.run, steps, warmup)
     g.close(); g2.close(); h.close()
     del items
@@ -863,6 +867,8 @@ def main():
                     help="default workload: skip the grouped and serving forms that follow plain_large")
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision", "grouped", "serving", "single"])
     ap.add_argument("--count", type=int, default=2048)
+    ap.add_argument("--method-s", default="auto", choices=["auto", "ffma", "tf32x3", "bf16x3"],
+                    help="grouped workload: method of the single-precision problems")
     ap.add_argument("--combo", default="dddd")
     ap.add_argument("--method", default="auto")
     ap.add_argument("--layout", default="col,col,col", help="storage of A,B,C: col | row | gen")

@@ -239,13 +239,20 @@ int mxg_check_device_error(mxg_handle h, int* flag);
  *
  * mxg_group_create validates and plans every problem (the first invalid one makes it
  * fail with that problem's status; *first_bad receives its index when first_bad is not
- * NULL), buckets the problems by computation precision, and builds on the device:
- * the packed operands of every problem, one pack work list per bucket and one
+ * NULL), buckets the problems by computation precision and method, and builds on the
+ * device: the packed operands of every problem, one pack work list per bucket and one
  * (problem, tile) work list per bucket, ordered longest-first. A run is then one
  * grouped pack launch and one persistent contraction launch per bucket (plus a
  * C := beta*C launch per problem with k == 0 or alpha == 0).
- *   method_s: MXG_METHOD_AUTO or MXG_METHOD_FFMA (single-precision bucket);
+ *   method_s: MXG_METHOD_AUTO or MXG_METHOD_FFMA (single precision on the FP32 pipe), or
+ *             MXG_METHOD_TF32X3 / MXG_METHOD_BF16X3 (single precision on the tensor
+ *             cores; problems below the method's smallest k, MXG_SPLIT_MIN_K_*, run in
+ *             the FFMA bucket instead);
  *   method_d: MXG_METHOD_AUTO (= DFMA), MXG_METHOD_DMMA or MXG_METHOD_DFMA (double bucket);
+ *   the 16-bit computation precisions run in two tensor-core buckets (TC16, binary16 and
+ *   bfloat16). Tensor-core buckets use each problem's own tensor maps, encoded at create
+ *   time, on a persistent 128 x 256-tile tcgen05 kernel; their bounded waits report a
+ *   timeout through the handle's error word (mxg_check_device_error);
  *   flags:    MXG_GROUP_TUNE  -- time each bucket's candidate kernels and schedules
  *                                 (into scratch copies of C, so the problems' C are not
  *                                 touched) and keep the fastest; decisions are cached in

@@ -25,6 +25,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "grouped.h"
 #include "tc_common.cuh"
 
 namespace mxg {
@@ -91,10 +92,56 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   *tn = r / gsz;
 }
 
-template <int SPLIT>
-__global__ void __launch_bounds__(192, 1)
-tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcArgs g) {
+// One tile of work for the tcgen05 body: the tensor maps of its operand planes, its
+// first rows of A' and B' (= its position in P), its number of k-blocks and the
+// epilogue it ends with.
+struct TcJob {
+  const CUtensorMap *ah, *al, *bh, *bl;
+  int32_t ym, yn;
+  int nkb;
+  const EpiArgs* e;
+  int cdt, mode;
+};
+
+// The tiles of one problem in the grouped order; maps and arguments are kernel
+// parameters.
+struct TcOneSrc {
+  const CUtensorMap *ah, *al, *bh, *bl;
+  const TcArgs* g;
+  int tiles_m, tiles_n, nkb;
+  __device__ __forceinline__ int count() const { return tiles_m * tiles_n; }
+  __device__ __forceinline__ TcJob job(int t) const {
+    int tm, tn;
+    tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+    return TcJob{ah, al, bh, bl, tm * TC_BM, tn * TC_BN, nkb, &g->e, g->cdt, g->mode};
+  }
+  __device__ __forceinline__ void prepare(const TcJob&) const {}
+};
+
+// The tiles of many problems, from a device work list (longest K' first); each problem's
+// maps were encoded on the host and copied to the device before the launch.
+struct TcGroupSrc {
+  const TcGroupProb* probs;
+  const GroupTile* tiles;
+  int ntiles, bk;
+  __device__ __forceinline__ int count() const { return ntiles; }
+  __device__ __forceinline__ TcJob job(int t) const {
+    const GroupTile w = tiles[t];
+    const TcGroupProb* p = probs + w.prob;
+    return TcJob{&p->maps[0], &p->maps[1], &p->maps[2], &p->maps[3], w.tm * TC_BM, w.tn * TC_BN,
+                 static_cast<int>(p->Kp / bk), &p->e, p->cdt, p->mode};
+  }
+  // order the TMA unit's reads of the maps after their copy to global memory
+  __device__ __forceinline__ void prepare(const TcJob& j) const {
+    const CUtensorMap* m[4] = {j.ah, j.al, j.bh, j.bl};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m[i]) : "memory");
+  }
+};
+
+template <int SPLIT, class Src>
+__device__ __forceinline__ void tc_body(const Src& src, int* err) {
   using F = TcFmt<SPLIT>;
   constexpr int TC_STAGES = F::stages;
   constexpr uint32_t STAGE_BYTES = F::stage_bytes;
@@ -114,9 +161,7 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   const uint32_t drain_bar = bars + 8u * (2 * TC_STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_m = static_cast<int>(g.Mp / TC_BM), tiles_n = static_cast<int>(g.Np / TC_BN);
-  const int ntiles = tiles_m * tiles_n;
-  const int nkb = static_cast<int>(g.Kp / BK);
+  const int ntiles = src.count();
 
   static_assert(2 * TC_STAGES + 5 <= static_cast<int>(NBARS_MAX), "barrier area");
   if (threadIdx.x == 0) {
@@ -143,7 +188,7 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   auto fail = [&]() {
-    if (g.err) atomicExch(g.err, 1);
+    if (err) atomicExch(err, 1);
     *abort_flag = 1;
   };
 
@@ -152,10 +197,10 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       uint32_t it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        int tm, tn;
-        tile_coords(t, tiles_m, tiles_n, &tm, &tn);
-        const int32_t ym = tm * TC_BM, yn = tn * TC_BN;
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const TcJob jb = src.job(t);
+        src.prepare(jb);
+        const int32_t ym = jb.ym, yn = jb.yn;
+        for (int kb = 0; kb < jb.nkb; ++kb, ++it) {
           const int s = static_cast<int>(it % TC_STAGES);
           const uint32_t use = it / TC_STAGES;
           if (!mbar_wait(empty(s), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -163,10 +208,10 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           mbar_expect_tx(full(s), STAGE_BYTES);
           const int32_t kx = kb * BK;
           // stage layout: A planes (F::planes x TILE_A), then B planes
-          tma_load_2d(st, &mAh, kx, ym, full(s));
-          if constexpr (F::planes == 2) tma_load_2d(st + TILE_A, &mAl, kx, ym, full(s));
-          tma_load_2d(st + F::planes * TILE_A, &mBh, kx, yn, full(s));
-          if constexpr (F::planes == 2) tma_load_2d(st + 2 * TILE_A + TILE_B, &mBl, kx, yn, full(s));
+          tma_load_2d(st, jb.ah, kx, ym, full(s));
+          if constexpr (F::planes == 2) tma_load_2d(st + TILE_A, jb.al, kx, ym, full(s));
+          tma_load_2d(st + F::planes * TILE_A, jb.bh, kx, yn, full(s));
+          if constexpr (F::planes == 2) tma_load_2d(st + 2 * TILE_A + TILE_B, jb.bl, kx, yn, full(s));
         }
       }
       if (!ok) {
@@ -186,6 +231,7 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         if (!mbar_wait(acc_empty(b), (static_cast<uint32_t>(j >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_tmem = tmem + static_cast<uint32_t>(b * TC_BN);
+        const int nkb = src.job(t).nkb;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = static_cast<int>(it % TC_STAGES);
           if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag)) { ok = false; break; }
@@ -217,8 +263,7 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     const int q = warp & 3;
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-      int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      const TcJob jb = src.job(t);
       const int b = j & 1;
       const bool ok = mbar_wait(acc_full(b), static_cast<uint32_t>(j >> 1) & 1u, abort_flag);
       if (!__all_sync(0xffffffffu, ok && !*abort_flag)) {
@@ -226,19 +271,20 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t m0 = static_cast<int64_t>(tm) * TC_BM, n0 = static_cast<int64_t>(tn) * TC_BN;
+      const int64_t m0 = jb.ym, n0 = jb.yn;
       const int64_t row = m0 + 32 * q + lane;
+      const EpiArgs& e = *jb.e;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b * TC_BN);
-      with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
+      with_c_mode(jb.cdt, jb.mode, [&](auto C, auto M) {
         constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
-        const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(g.e);
+        const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(e);
 #pragma unroll 1
         for (int c0 = 0; c0 < TC_BN; c0 += 32) {
           COld<CDT> old[TcChunk<MODE>::nold];
-          tc_epi_load<CDT, MODE>(g.e, row, n0 + c0, lane, old);
+          tc_epi_load<CDT, MODE>(e, row, n0 + c0, lane, old);
           uint32_t v[32];
           tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-          tc_epi_finish<CDT, MODE>(g.e, sc, row, n0 + c0, v, lane, old);
+          tc_epi_finish<CDT, MODE>(e, sc, row, n0 + c0, v, lane, old);
         }
       });
       // release the accumulator to the MMA warp
@@ -253,6 +299,26 @@ tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+}
+
+
+template <int SPLIT>
+__global__ void __launch_bounds__(192, 1)
+tc_split_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+              const __grid_constant__ TcArgs g) {
+  constexpr int BK = ROWB / TcFmt<SPLIT>::elem;
+  const TcOneSrc src{&mAh, &mAl, &mBh, &mBl, &g, static_cast<int>(g.Mp / TC_BM), static_cast<int>(g.Np / TC_BN),
+                     static_cast<int>(g.Kp / BK)};
+  tc_body<SPLIT>(src, g.err);
+}
+
+// Grouped form: a persistent launch over the (problem, tile) work list of a bucket.
+template <int SPLIT>
+__global__ void __launch_bounds__(192, 1)
+tc_grouped_gemm(const TcGroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int ntiles, int* err) {
+  const TcGroupSrc src{probs, tiles, ntiles, static_cast<int>(ROWB / TcFmt<SPLIT>::elem)};
+  tc_body<SPLIT>(src, err);
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing will
@@ -347,6 +413,45 @@ bool tc_make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int
   return make_map(map, ptr, split, rows, Kp, rows_box, rowb);
 }
 cudaError_t tc_current_sm_count(int* out) { return current_sm_count(out); }
+
+bool tc_group_problem(TcGroupProb* p, int split, const void* const planes[4], int64_t Mp, int64_t Np, int64_t Kp,
+                      const EpiArgs& e, int cdt, int mode) {
+  if (!get_encoder()) return false;
+  const int bk = static_cast<int>(ROWB) / (split == SPLIT_TF32 ? 4 : 2);
+  if (Mp % TC_BM || Np % TC_BN || Kp % bk || Mp <= 0 || Np <= 0 || Kp <= 0) return false;
+  if (!make_map(&p->maps[0], planes[0], split, Mp, Kp, TC_BM) || !make_map(&p->maps[1], planes[1], split, Mp, Kp, TC_BM) ||
+      !make_map(&p->maps[2], planes[2], split, Np, Kp, TC_BN) || !make_map(&p->maps[3], planes[3], split, Np, Kp, TC_BN))
+    return false;
+  p->Mp = Mp; p->Np = Np; p->Kp = Kp;
+  p->e = e;
+  p->cdt = cdt;
+  p->mode = mode;
+  bool valid = false;
+  with_c_mode(cdt, mode, [&](auto, auto) { valid = true; });
+  return valid;
+}
+
+cudaError_t launch_gemm_tc_grouped(int split, const TcGroupProb* probs, const GroupTile* tiles, int ntiles, int* err,
+                                   cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  int sms = 0;
+  cudaError_t e = current_sm_count(&sms);
+  if (e != cudaSuccess) return e;
+  const int grid = ntiles < sms ? ntiles : sms;
+  auto go = [&](auto kern) {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (r != cudaSuccess) return r;
+    kern<<<grid, 192, TC_SMEM, s>>>(probs, tiles, ntiles, err);
+    return cudaGetLastError();
+  };
+  switch (split) {
+    case SPLIT_TF32: return go(tc_grouped_gemm<SPLIT_TF32>);
+    case SPLIT_BF16: return go(tc_grouped_gemm<SPLIT_BF16>);
+    case SPLIT_F16_ONE: return go(tc_grouped_gemm<SPLIT_F16_ONE>);
+    case SPLIT_BF16_ONE: return go(tc_grouped_gemm<SPLIT_BF16_ONE>);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s) {
   wait_timeout_probe<<<1, 32, 0, s>>>(err, static_cast<unsigned long long>(seconds * 1e9));

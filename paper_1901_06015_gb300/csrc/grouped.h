@@ -1,6 +1,8 @@
 // Device work lists and launchers of the grouped persistent launch.
 #pragma once
 
+#include <cuda.h>
+
 #include <vector>
 
 #include "mxg_internal.h"
@@ -37,6 +39,16 @@ struct GroupTile {
   int tm, tn;          // tile coordinates in units of the variant's tile
 };
 
+// One problem of a tensor-core bucket (TF32X3, BF16X3 or TC16): the tensor maps of its
+// K-major planes (A hi, A lo, B hi, B lo; the one-plane formats repeat the hi maps),
+// encoded on the host, and its epilogue. Tiles are 128 x 256.
+struct alignas(64) TcGroupProb {
+  CUtensorMap maps[4];
+  int64_t Mp, Np, Kp;  // padded real problem
+  EpiArgs e;
+  int cdt, mode;
+};
+
 #ifdef __CUDACC__
 // Fetch the next work-list index for the whole CTA (dynamic schedule: one atomic per
 // tile on the bucket's counter; static schedule: CTA b takes b, b + grid, ...).
@@ -68,6 +80,16 @@ int grouped_blocks_per_sm(int variant);
 cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const GroupTile* tiles, int ntiles,
                                 int* counter, int sched, int grid, cudaStream_t s);
 int64_t pack_tiles(const PackArgs& a);
+// Grouped pack into the K-major planes of one tensor-core format (SplitKind).
+cudaError_t launch_pack_grouped_tc(const PackArgs* tasks, const int64_t* tile_start, int ntasks, int64_t ntiles,
+                                   int split, cudaStream_t s);
+// Encode the four maps of a tensor-core problem (planes as for launch_gemm_tc).
+bool tc_group_problem(TcGroupProb* p, int split, const void* const planes[4], int64_t Mp, int64_t Np, int64_t Kp,
+                      const EpiArgs& e, int cdt, int mode);
+// Persistent tcgen05 contraction over a bucket's work list (static schedule, 128 x 256
+// tiles, one CTA per SM); err: the device error word for wait timeouts.
+cudaError_t launch_gemm_tc_grouped(int split, const TcGroupProb* probs, const GroupTile* tiles, int ntiles, int* err,
+                                   cudaStream_t s);
 cudaError_t launch_pack_grouped(const PackArgs* tasks, const int64_t* tile_start, int ntasks, int64_t ntiles,
                                 int comp_double, cudaStream_t s);
 

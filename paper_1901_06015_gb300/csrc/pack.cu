@@ -273,8 +273,10 @@ __global__ void __launch_bounds__(256, 5) pack_kernel(PackArgs a, int64_t ntile_
 
 // Grouped pack: block b packs tile (b - tile_start[t]) of task t, where t is found by a
 // binary search of the tile prefix sums; the tasks' source datatypes and patterns
-// differ, so both are dispatched at run time (uniformly over the block).
-template <typename DT>
+// differ, so both are dispatched at run time (uniformly over the block). The layout and
+// plane format are the bucket's: MN-major for the SIMT / DMMA kernels, or the K-major
+// planes of one tensor-core format.
+template <typename DT, int LAYOUT, int SPLIT>
 __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __restrict__ tasks,
                                                            const int64_t* __restrict__ tile_start, int ntasks) {
   __shared__ PackSmem<DT> sm;
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(256) pack_grouped_kernel(const PackArgs* __res
   auto run = [&](auto S) {
     constexpr int SDT = decltype(S)::value;
     with_pattern<SDT>(a.pattern, [&](auto P) {
-      pack_tile<SDT, DT, LAYOUT_MN_MAJOR, SPLIT_NONE, decltype(P)::value>(a, mn0, p0, sm);
+      pack_tile<SDT, DT, LAYOUT, SPLIT, decltype(P)::value>(a, mn0, p0, sm);
     });
   };
   switch (a.src_dt) {
@@ -350,8 +352,37 @@ cudaError_t launch_pack_grouped(const PackArgs* tasks, const int64_t* tile_start
                                 int comp_double, cudaStream_t s) {
   if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (comp_double) pack_grouped_kernel<double><<<static_cast<unsigned>(ntiles), 256, 0, s>>>(tasks, tile_start, ntasks);
-  else pack_grouped_kernel<float><<<static_cast<unsigned>(ntiles), 256, 0, s>>>(tasks, tile_start, ntasks);
+  const unsigned grid = static_cast<unsigned>(ntiles);
+  if (comp_double)
+    pack_grouped_kernel<double, LAYOUT_MN_MAJOR, SPLIT_NONE><<<grid, 256, 0, s>>>(tasks, tile_start, ntasks);
+  else
+    pack_grouped_kernel<float, LAYOUT_MN_MAJOR, SPLIT_NONE><<<grid, 256, 0, s>>>(tasks, tile_start, ntasks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_grouped_tc(const PackArgs* tasks, const int64_t* tile_start, int ntasks, int64_t ntiles,
+                                   int split, cudaStream_t s) {
+  if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const unsigned grid = static_cast<unsigned>(ntiles);
+  // the split forms cast to single precision first; the one-plane 16-bit formats round
+  // once from a double working type (exact for every source, so the same rounding as
+  // the single-problem pack's source-precision working type)
+  switch (split) {
+    case SPLIT_TF32:
+      pack_grouped_kernel<float, LAYOUT_K_MAJOR, SPLIT_TF32><<<grid, 256, 0, s>>>(tasks, tile_start, ntasks);
+      break;
+    case SPLIT_BF16:
+      pack_grouped_kernel<float, LAYOUT_K_MAJOR, SPLIT_BF16><<<grid, 256, 0, s>>>(tasks, tile_start, ntasks);
+      break;
+    case SPLIT_F16_ONE:
+      pack_grouped_kernel<double, LAYOUT_K_MAJOR, SPLIT_F16_ONE><<<grid, 256, 0, s>>>(tasks, tile_start, ntasks);
+      break;
+    case SPLIT_BF16_ONE:
+      pack_grouped_kernel<double, LAYOUT_K_MAJOR, SPLIT_BF16_ONE><<<grid, 256, 0, s>>>(tasks, tile_start, ntasks);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -75,7 +75,7 @@ def test_16bit_sampled_blocks_4096(combo):
 
 def test_16bit_storage_in_grouped_and_served_forms():
     """16-bit storage with single/double computation runs in a grouped launch; a 16-bit
-    computation precision is served (per call) but not grouped (MXG_ENOTSUP)."""
+    computation precision runs in the group's TC16 buckets and is served per call."""
     import paper_1901_06015_gb300 as mx
     combos = ["hsss", "sbbs", "kkcd", "wzwd", "hhhs", "bdbd"]
     probs = [synth.problem(40 + i, c, 50 + 7 * i, 40, 60) for i, c in enumerate(combos)]
@@ -90,9 +90,14 @@ def test_16bit_storage_in_grouped_and_served_forms():
         assert err <= tolerance(c, 60), (c, err)
     g.close()
     A, B, C0 = synth.problem(50, "hhhh", 30, 20, 40)
-    with pytest.raises(mx.MxgError) as e:
-        mx.Group([("n", "n", 1.0, to_device(A), to_device(B), 0.0, to_device(C0), "h")], tune=False, graph=False)
-    assert e.value.status == 6
+    dC = to_device(C0)
+    g = mx.Group([("n", "n", 1.0, to_device(A), to_device(B), 0.0, dC, "h")], tune=False, graph=False)
+    g.run()
+    torch.cuda.synchronize()
+    g.close()
+    ref = oracle_mxgemm("n", "n", 1.0, A, B, 0.0, C0.copy(), comp="h")
+    err, _ = normwise_error("hhhh", from_device(dC, "h"), ref, A, B, C0, 1.0, 0.0)
+    assert err <= tolerance("hhhh", 40, "tc16")
     srv = mx.Server(n_streams=2, hbm_budget_bytes=1 << 28)
     dA, dB, dC = to_device(A), to_device(B), to_device(C0)
     srv.submit(("n", "n", 1.0, dA, dB, 0.0, dC, "h"))

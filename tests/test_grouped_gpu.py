@@ -210,3 +210,59 @@ def test_grouped_batching_configuration_sampled_blocks():
         err, _ = normwise_error(combo, got, ref, Ab, Bb, C0, 1.5, -0.5)
         assert err <= tolerance(combo, k), (combo, k, err)
     g.close()
+
+
+def _solo16(p, meth):
+    """p run alone through mxgemm_ex with method meth; C as numpy (16-bit aware)."""
+    import paper_1901_06015_gb300 as mx
+    from tests.gpu_util import from_device
+    dA, dB, dC = to_device(p["A"]), to_device(p["B"]), to_device(p["C"])
+    mx.mxgemm_ex(None, meth, p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, comp=p["combo"][3])
+    torch.cuda.synchronize()
+    return from_device(dC, p["combo"][0])
+
+
+@pytest.mark.parametrize("method_s", ["bf16x3", "tf32x3"])
+def test_grouped_tensor_core_buckets(method_s):
+    """Tensor-core buckets of a grouped launch: single-precision problems on the split
+    method (those below its smallest k fall back to the FFMA bucket), the 16-bit
+    computation precisions on TC16, next to the plain buckets, graph-captured and timed.
+    Every result equals the same problem run alone with its method bit for bit and is
+    within the stated bound of the oracle."""
+    import paper_1901_06015_gb300 as mx
+    from tests.gpu_util import from_device
+    from tests._helpers import SPLIT_MIN_K, comp_prec
+    rng = np.random.default_rng(5)
+    combos = ["ssss", "cscs", "zcds", "dsss", "zzzs", "czcs", "hhhh", "kkkh", "bbbb", "wbwb", "shhh", "zbbb",
+              "dddd", "zzzd", "ccsd"]
+    probs = []
+    for i in range(45):
+        combo = combos[i % len(combos)]
+        m, n = (int(x) for x in rng.integers(20, 300, size=2))
+        k = int(rng.choice([40, 200, 330, 700]))
+        ta, tb = "ntch"[i % 4], "nt"[i % 2]
+        A, B, C = synth.problem(700 + i, combo, m, n, k, transa=ta, transb=tb, order_c="FC"[i % 2])
+        alpha = complex(1.25, -0.5) if all(synth.is_complex(c) for c in combo[:3]) else 1.5
+        beta = (0.5 - 0.25j) if synth.is_complex(combo[0]) else -0.5
+        probs.append(dict(combo=combo, ta=ta, tb=tb, alpha=alpha, beta=beta, A=A, B=B, C=C, k=k))
+    dev = [(to_device(p["A"]), to_device(p["B"]), to_device(p["C"])) for p in probs]
+    items = [(p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, p["combo"][3]) for p, (dA, dB, dC) in zip(probs, dev)]
+    g = mx.Group(items, method_s=method_s, tune=True, graph=True)
+    g.run()
+    torch.cuda.synchronize()
+    kernels = {b["kernel"] for b in g.describe()["buckets"]}
+    assert {"tc16_f16", "tc16_bf16", "tc_" + method_s} <= kernels, kernels
+    h = mx.Handle()
+    h.set_stream(torch.cuda.current_stream())
+    assert h.check_device_error() == 0
+    for p, (_, _, dC) in zip(probs, dev):
+        x = comp_prec(p["combo"])
+        meth = "tc16" if x in "hb" else ("dfma" if x == "d" else (method_s if p["k"] >= SPLIT_MIN_K[method_s] else "ffma"))
+        got = from_device(dC, p["combo"][0])
+        assert np.array_equal(synth.to_c128(got), synth.to_c128(_solo16(p, meth))), (p["combo"], meth)
+        ref = oracle_mxgemm(p["ta"], p["tb"], p["alpha"], p["A"], p["B"], p["beta"], np.array(p["C"], order="K"),
+                            comp=p["combo"][3])
+        err, _ = normwise_error(p["combo"], got, ref, p["A"], p["B"], p["C"], p["alpha"], p["beta"], p["ta"], p["tb"])
+        assert err <= tolerance(p["combo"], p["k"], meth, p["beta"]), (p["combo"], meth, err)
+    g.close()
+    h.close()
