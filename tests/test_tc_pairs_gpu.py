@@ -56,3 +56,36 @@ def test_pairs_equal_single_cta_and_oracle(combo, shape, method):
     err, _ = normwise_error(combo, got_p, ref, A, B, C0, alpha, beta)
     assert err <= tolerance(combo, k, method, beta), (combo, method, err)
     hp.close(); hs.close()
+
+
+@pytest.mark.parametrize("combo,method", [("ssss", "bf16x3"), ("hhhh", "tc16"), ("zcds", "tf32x3")])
+def test_pairs_wide_tiles_equal_single_cta(combo, method):
+    """A problem with enough 256 x 256 pair tiles to fill the device (128 pair tiles on
+    76 pairs of SMs, two waves): bit-equal to the single-CTA kernel, and the first 64 x 64
+    block within the bound of the oracle."""
+    import paper_1901_06015_gb300 as mx
+    m, n, k = 2048, 4096, 320
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(9)
+    A = synth.torch_matrix(gen, m, k, combo[1], "cuda")
+    B = synth.torch_matrix(gen, k, n, combo[2], "cuda")
+    C0 = synth.torch_matrix(gen, m, n, combo[0], "cuda")
+    outs = []
+    for mode in (1, 2):
+        h = mx.Handle()
+        h.set_stream(torch.cuda.current_stream())
+        h.set_cta_pairs(mode)
+        C = C0.clone()
+        mx.mxgemm_ex(h, method, "n", "n", 1.0, A, B, 1.0, C, comp=combo[3])
+        torch.cuda.synchronize()
+        assert h.check_device_error() == 0
+        outs.append(C)
+        h.close()
+    assert torch.equal(outs[0], outs[1])
+    Ab = from_device(A[:64, :], combo[1])
+    Bb = from_device(B[:, :64], combo[2])
+    Cb = from_device(C0[:64, :64], combo[0])
+    ref = oracle_mxgemm("n", "n", 1.0, np.asfortranarray(Ab), np.asfortranarray(Bb), 1.0,
+                        np.asfortranarray(Cb.copy()), comp=combo[3])
+    err, _ = normwise_error(combo, from_device(outs[0][:64, :64], combo[0]), ref, Ab, Bb, Cb, 1.0, 1.0)
+    assert err <= tolerance(combo, k, method), (combo, err)
