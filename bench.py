@@ -360,6 +360,9 @@ def run_ours(args):
         "kernel": kname, "bound": "tensor", "achieved": ach_d, "peak": fp64_peak, "unit": "TFLOP/s",
         "frac": (ach_d / fp64_peak) if ach_d else None,
         "traffic": traffic_per_launch(kname),
+        "traffic_note": "scaled, not captured at this size: DRAM bytes of one ncu capture of the kernel at "
+                        "4096^3 (dddd, profiles/traffic.json) times the useful-flop ratio of the mean launch here "
+                        "(2*8192^3*1.75 flops); null once the kernel's source changes",
         "peak_source": f"{peak_src} bf16_tflops_sustained x nominal FP64/BF16 ratio (1.25/2250); "
                        "kernel timed inside a long step",
         "share_of_step": con_d / ms if ms else None,
