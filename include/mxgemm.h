@@ -225,9 +225,12 @@ int mxg_set_stream(mxg_handle h, void* stream);
  * must not reuse the memory until work enqueued on h has completed. */
 int mxg_set_workspace(mxg_handle h, void* ptr, size_t bytes);
 
-/* Device error word of h: nonzero if a device-side wait ran out of its iteration
- * limit since the last call to this function (which clears it). Synchronises h's
- * stream. Returns MXG_OK or MXG_ECUDA; *flag receives the word. */
+/* Device error word of h: nonzero if something went wrong on the device since the last
+ * call to this function (which clears it): bit 0 (1) a device-side wait ran out of its
+ * iteration limit; bit 1 (2), debug builds only (mxg_debug_bounds), a pack kernel or an
+ * epilogue computed an element address outside the extent its arguments describe and
+ * skipped that access. Synchronises h's stream. Returns MXG_OK or MXG_ECUDA; *flag
+ * receives the word. */
 int mxg_check_device_error(mxg_handle h, int* flag);
 
 /*
@@ -423,6 +426,11 @@ int mxg_last_cuda_error(void);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int mxg_version(void);
+
+/* 1 if this library is the debug build with device-side bounds checks of every pack and
+ * epilogue access (compiled with MXG_DEBUG_BOUNDS; violations set bit 1 of the device
+ * error word instead of touching memory), else 0. */
+int mxg_debug_bounds(void);
 
 #ifdef __cplusplus
 }

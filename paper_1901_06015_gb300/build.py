@@ -16,6 +16,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmxgemm.so")
+# Debug build: the same library compiled with -DMXG_DEBUG_BOUNDS, whose pack kernels and
+# epilogues check every element address against the extent their arguments describe and
+# report a violation in the device error word (mxg_check_device_error) instead of
+# accessing it. Built on request only (build(debug_bounds=True)).
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libmxgemm_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,23 +40,26 @@ def _deps():
         [os.path.join(ROOT, "include", "mxgemm.h"), os.path.abspath(__file__)]
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(debug_bounds=False):
+    lib = LIB_DEBUG if debug_bounds else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force=False, verbose=False):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, debug_bounds=False):
+    lib_path = LIB_DEBUG if debug_bounds else LIB
+    build_dir = BUILD_DEBUG if debug_bounds else BUILD
+    if not force and up_to_date(debug_bounds):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default",
-              "-I", os.path.join(ROOT, "include")]
+              "-I", os.path.join(ROOT, "include")] + (["-DMXG_DEBUG_BOUNDS"] if debug_bounds else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
             cmd = [nvcc] + ARCH + common + ["-lineinfo", "--expt-relaxed-constexpr", "-c", src, "-o", obj]
         else:
@@ -65,14 +74,14 @@ def build(force=False, verbose=False):
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + \
         ["-Xlinker", "--version-script=" + os.path.join(CSRC, "exports.map")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

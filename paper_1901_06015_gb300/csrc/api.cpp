@@ -233,7 +233,7 @@ static void operand_strides_b(const Call& w, int64_t* smn, int64_t* sk) {
 }
 
 EpiArgs plan_epilogue(const Plan& P) {
-  EpiArgs e;
+  EpiArgs e{};
   const Call& w = (P.kind == PLAN_GEMM) ? P.work : P.call;
   e.C = w.C; e.rs = w.rsC; e.cs = w.csC; e.m = w.m; e.n = w.n;
   e.ar = P.ar; e.ai = P.ai; e.br = P.br; e.bi = P.bi; e.beta_zero = P.beta_zero;
@@ -246,6 +246,7 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   if (P.kind == PLAN_SCALE) {
     EpiArgs e = plan_epilogue(P);
     e.ar = 0.0; e.ai = 0.0;
+    e.dbg = dev_err;
     return cuda_status(launch_scale_c(e, P.call.dtC, s));
   }
   const Call& w = P.work;
@@ -257,6 +258,7 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   pa.dst = base; pa.dst_lo = nullptr; pa.ld = P.Mp; pa.MNp = P.Mp; pa.Kp = P.Kp;
   pa.layout = LAYOUT_MN_MAJOR; pa.split = SPLIT_NONE;
   pa.fold = P.fold_a; pa.fold_re = P.ar; pa.fold_im = P.ai;
+  pa.dbg = dev_err;
   if (P.split != SPLIT_NONE) {
     pa.dst_lo = (P.method == MXG_METHOD_TC16) ? nullptr : base + P.plane_a;
     pa.ld = P.Kp; pa.layout = LAYOUT_K_MAJOR; pa.split = P.split;
@@ -270,6 +272,7 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   pb.dst = base + P.bytes_a; pb.dst_lo = nullptr; pb.ld = P.Np; pb.MNp = P.Np; pb.Kp = P.Kp;
   pb.layout = LAYOUT_MN_MAJOR; pb.split = SPLIT_NONE;
   pb.fold = P.fold_b; pb.fold_re = P.ar; pb.fold_im = P.ai;
+  pb.dbg = dev_err;
   if (P.split != SPLIT_NONE) {
     pb.dst_lo = (P.method == MXG_METHOD_TC16) ? nullptr : base + P.bytes_a + P.plane_b;
     pb.ld = P.Kp; pb.layout = LAYOUT_K_MAJOR; pb.split = P.split;
@@ -277,19 +280,21 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
   st = cuda_status(launch_pack(pb, P.comp_double, s));
   if (st) return st;
   if (ev_mid) cudaEventRecord(ev_mid, s);
+  EpiArgs ep = plan_epilogue(P);
+  ep.dbg = dev_err;
   if (P.split != SPLIT_NONE) {
     const bool one = (P.method == MXG_METHOD_TC16);
     const void* planes[4] = {base, one ? base : base + P.plane_a, base + P.bytes_a,
                              one ? base + P.bytes_a : base + P.bytes_a + P.plane_b};
     const cudaError_t e =
-        P.pairs ? launch_gemm_tc_pair(P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P), dev_err, s)
-                : launch_gemm_tc(P.method, P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P), dev_err,
+        P.pairs ? launch_gemm_tc_pair(P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, ep, dev_err, s)
+                : launch_gemm_tc(P.method, P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, ep, dev_err,
                                  s);
     return e == cudaErrorNotSupported ? MXG_ENOTSUP : cuda_status(e);
   }
   GemmArgs g;
   g.A = base; g.B = base + P.bytes_a; g.lda = P.Mp; g.ldb = P.Np; g.Kp = P.Kp;
-  g.Mp = P.Mp; g.Np = P.Np; g.e = plan_epilogue(P);
+  g.Mp = P.Mp; g.Np = P.Np; g.e = ep;
   if (P.splits > 1)
     return cuda_status(launch_gemm_splitk(P.method, w.dtC, P.mode, g, P.splits, P.kslice,
                                           base + P.bytes_a + P.bytes_b, s));
@@ -349,6 +354,14 @@ static int default_handle(mxg_context** out) {
 extern "C" {
 
 int mxg_version(void) { return 10000; }
+
+int mxg_debug_bounds(void) {
+#ifdef MXG_DEBUG_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 int mxg_last_cuda_error(void) { return g_last_cuda_error; }
 

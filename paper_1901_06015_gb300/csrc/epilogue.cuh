@@ -72,6 +72,17 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_ct<__nv_bfloat16>(float 
 template <> __device__ __forceinline__ __nv_bfloat16 to_ct<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
 
 
+// Debug builds: does the element at c lie inside the storage that (m, n, rs, cs)
+// describe for C (first element to the last one, both parts of a complex element)?
+template <int CDT>
+__device__ __forceinline__ bool c_in_extent(const EpiArgs& e, const void* c) {
+  using CT = typename CStore<CDT>::T;
+  const int64_t w = CStore<CDT>::cplx ? 2 : 1;
+  const int64_t off = static_cast<const CT*>(c) - static_cast<const CT*>(e.C);
+  const int64_t last = ((e.m - 1) * e.rs + (e.n - 1) * e.cs) * w + (w - 1);
+  return off >= 0 && off + (w - 1) <= last;
+}
+
 // C's value at (i, j) before the update, in C's storage type (im = 0 for a real C);
 // zero, and not read, where beta == 0 or (i, j) lies outside C. The kernels read a
 // thread's group of C elements with epi_load first and then update them with
@@ -85,6 +96,7 @@ __device__ __forceinline__ COld<CDT> epi_load(const EpiArgs& e, int64_t i, int64
   COld<CDT> o{to_ct<CT>(0.0f), to_ct<CT>(0.0f)};
   if (e.beta_zero || i >= e.m || j >= e.n) return o;
   const CT* c = static_cast<const CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
+  if (!MXG_DBG_OK(c_in_extent<CDT>(e, c), e.dbg)) return o;
   o.re = c[0];
   if constexpr (CStore<CDT>::cplx) o.im = c[1];
   return o;
@@ -119,6 +131,7 @@ __device__ __forceinline__ void epi_update(const EpiArgs& e, const EpiScalars<Ac
   using CT = typename CStore<CDT>::T;
   if (i >= e.m || j >= e.n) return;
   CT* c = static_cast<CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
+  if (!MXG_DBG_OK(c_in_extent<CDT>(e, c), e.dbg)) return;
   if constexpr (!CStore<CDT>::cplx) {
     // C real: alpha and beta projected onto the real line (Sec. 7.2).
     const CT t = to_ct<CT>(mul_rn(sc.ar, pr));

@@ -41,7 +41,7 @@ std::vector<GroupTile> group_tiles(const std::vector<GroupProb>& probs, int vari
   return out;
 }
 
-void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta, PackArgs* tb) {
+void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta, PackArgs* tb, int* dbg) {
   const Call& w = P.work;
   char* pb = pa + P.bytes_a;
   *gp = GroupProb{};
@@ -62,6 +62,7 @@ void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta
   else { tb->smn = w.csB; tb->sk = w.rsB; }
   tb->MN = w.n; tb->K = w.k; tb->pattern = P.pat_b; tb->conj = P.conj_b;
   tb->dst = pb; tb->ld = P.Np; tb->MNp = P.Np; tb->Kp = P.Kp; tb->layout = LAYOUT_MN_MAJOR; tb->split = SPLIT_NONE;
+  gp->e.dbg = ta->dbg = tb->dbg = dbg;
 }
 
 }  // namespace mxg
@@ -186,6 +187,7 @@ int enqueue_run(mxg_group_s* g, cudaStream_t s, bool packs, bool gemms, const Bu
         const Plan& P = g->plans[i];
         EpiArgs e = plan_epilogue(P);
         e.ar = 0.0; e.ai = 0.0;
+        e.dbg = g->h->dev_err;
         int st = cstat(launch_scale_c(e, P.call.dtC, s));
         if (st) return st;
       }
@@ -360,7 +362,7 @@ void free_group(mxg_group_s* g) {
 
 // The four K-major planes of a planned tensor-core problem whose packs start at pa
 // (A hi, A lo, B hi, B lo; the one-plane formats repeat hi), and its two pack tasks.
-void tc_describe_problem(const Plan& P, char* pa, const void* planes[4], PackArgs* ta, PackArgs* tb) {
+void tc_describe_problem(const Plan& P, char* pa, const void* planes[4], PackArgs* ta, PackArgs* tb, int* dbg) {
   const Call& w = P.work;
   const bool one = (P.method == MXG_METHOD_TC16);
   char* pb = pa + P.bytes_a;
@@ -382,6 +384,7 @@ void tc_describe_problem(const Plan& P, char* pa, const void* planes[4], PackArg
   tb->MN = w.n; tb->K = w.k; tb->pattern = P.pat_b; tb->conj = P.conj_b;
   tb->dst = pb; tb->dst_lo = one ? nullptr : pb + P.plane_b;
   tb->ld = P.Kp; tb->MNp = P.Np; tb->Kp = P.Kp; tb->layout = LAYOUT_K_MAJOR; tb->split = P.split;
+  ta->dbg = tb->dbg = dbg;
 }
 
 int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int method_s, int method_d, int flags,
@@ -510,11 +513,13 @@ int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int metho
       PackArgs ta{}, tb{};
       if (tc) {
         const void* planes[4];
-        tc_describe_problem(P, base + pack_off[b.members[j]], planes, &ta, &tb);
-        if (!tc_group_problem(&b.tcprobs[j], P.split, planes, P.Mp, P.Np, P.Kp, plan_epilogue(P), P.work.dtC, P.mode))
+        tc_describe_problem(P, base + pack_off[b.members[j]], planes, &ta, &tb, h->dev_err);
+        EpiArgs ep = plan_epilogue(P);
+        ep.dbg = h->dev_err;
+        if (!tc_group_problem(&b.tcprobs[j], P.split, planes, P.Mp, P.Np, P.Kp, ep, P.work.dtC, P.mode))
           return MXG_ENOTSUP;
       } else {
-        group_describe_problem(P, base + pack_off[b.members[j]], &b.probs[j], &ta, &tb);
+        group_describe_problem(P, base + pack_off[b.members[j]], &b.probs[j], &ta, &tb, h->dev_err);
       }
       for (const PackArgs& t : {ta, tb}) {
         b.tasks.push_back(t);

@@ -68,7 +68,8 @@ struct Plan;
 // The grouped-launch description of one planned problem (PLAN_GEMM on the SIMT / DMMA
 // layout) whose packed operands start at pa (A' then B'): its GroupProb and its two
 // pack tasks.
-void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta, PackArgs* tb);
+// dbg: error word of the debug builds' bounds checks (may be null).
+void group_describe_problem(const Plan& P, char* pa, GroupProb* gp, PackArgs* ta, PackArgs* tb, int* dbg);
 // Work list of (problem, tile) for a variant, ordered longest-K' first.
 std::vector<GroupTile> group_tiles(const std::vector<GroupProb>& probs, int variant);
 cudaError_t launch_dmma(int mode, int cdt, const GemmArgs& g, cudaStream_t s, dim3 grid);

@@ -67,6 +67,7 @@ struct PackArgs {
   int split;         // SplitKind
   int fold;          // multiply each element by (fold_re + i fold_im) before the pattern
   double fold_re, fold_im;
+  int* dbg;          // debug builds (MXG_DEBUG_BOUNDS): error word for out-of-extent accesses
 };
 
 struct EpiArgs {
@@ -76,7 +77,20 @@ struct EpiArgs {
   double ar, ai;     // alpha, already rounded to the computation precision
   double br, bi;     // beta, already rounded to C's storage precision
   int beta_zero;     // C is not read
+  int* dbg;          // debug builds (MXG_DEBUG_BOUNDS): error word for out-of-extent accesses
 };
+
+// Debug builds (compiled with -DMXG_DEBUG_BOUNDS, see build.py) check every element
+// address the pack kernels read and write and every C address the epilogues read and
+// write against the extent its arguments describe, and OR MXG_DEBUG_BOUNDS_FLAG into
+// the error word when one falls outside (the access is then skipped). No trap: the
+// host reads the word (mxg_check_device_error). Normal builds compile the checks out.
+constexpr int MXG_DEBUG_BOUNDS_FLAG = 2;
+#if defined(MXG_DEBUG_BOUNDS) && defined(__CUDACC__)
+#define MXG_DBG_OK(cond, word) (((cond)) ? true : (((word) ? atomicOr((word), MXG_DEBUG_BOUNDS_FLAG) : 0), false))
+#else
+#define MXG_DBG_OK(cond, word) true
+#endif
 
 struct GemmArgs {
   const void* A;     // packed A' (comp precision), MN-major, Kp x lda

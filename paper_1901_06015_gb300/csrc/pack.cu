@@ -125,13 +125,23 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
   const int dm = unit_mn ? 0 : 8, dp = unit_mn ? 4 : 0;
   ST vr[8], vi[8];
   const ST* src = static_cast<const ST*>(a.src);
+#ifdef MXG_DEBUG_BOUNDS
+  // last stored component of the source operand: (MN-1, K-1), imaginary part included
+  const int64_t src_last = ((a.MN - 1) * a.smn + (a.K - 1) * a.sk) * CM + (CM - 1);
+#endif
   if (mn0 + PK_MN <= a.MN && p0 + PK_P <= a.K) {
     const ST* sp = src + ((mn0 + lm0) * a.smn + (p0 + lp0) * a.sk) * CM;
     const int64_t step = (dm * a.smn + dp * a.sk) * CM;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      vr[i] = __ldg(sp + i * step);
-      if constexpr (SC) vi[i] = __ldg(sp + i * step + 1);
+      const ST* q = sp + i * step;
+      if (!MXG_DBG_OK(q >= src && q + (CM - 1) - src <= src_last, a.dbg)) {
+        vr[i] = ST(0.0f);
+        vi[i] = ST(0.0f);
+        continue;
+      }
+      vr[i] = __ldg(q);
+      if constexpr (SC) vi[i] = __ldg(q + 1);
     }
   } else {
 #pragma unroll
@@ -141,6 +151,7 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
       vi[i] = ST(0.0f);
       if (mn < a.MN && p < a.K) {
         const ST* sp = src + (mn * a.smn + p * a.sk) * CM;
+        if (!MXG_DBG_OK(sp >= src && sp + (CM - 1) - src <= src_last, a.dbg)) continue;
         vr[i] = __ldg(sp);
         if constexpr (SC) vi[i] = __ldg(sp + 1);
       }
@@ -177,6 +188,8 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
       const int r = idx / VPR, c0 = (idx % VPR) * V;
       const int64_t kk = p0 * FK + r, mm = mn0 * FM + c0;
       if (kk >= a.Kp || mm >= a.MNp) continue;
+      // the packed operand is Kp rows of ld elements; a vector lies inside it
+      if (!MXG_DBG_OK(mm + V <= a.ld && kk * a.ld + mm + V <= a.Kp * a.ld, a.dbg)) continue;
       DT v[V];
 #pragma unroll
       for (int u = 0; u < V; ++u) v[u] = value(r, c0 + u);
@@ -192,6 +205,8 @@ __device__ __forceinline__ void pack_tile(const PackArgs& a, int64_t mn0, int64_
       const int64_t kk = p0 * FK + r0, mm = mn0 * FM + c;
       if (kk >= a.Kp || mm >= a.MNp) continue;
       const int64_t off = mm * a.ld + kk;
+      // the packed planes are MNp rows of ld elements; a vector lies inside them
+      if (!MXG_DBG_OK(kk + V <= a.ld && off + V <= a.MNp * a.ld, a.dbg)) continue;
       if constexpr (SPLIT == SPLIT_F16_ONE || SPLIT == SPLIT_BF16_ONE) {
         // one plane rounded once from the working type (TC16)
         uint4 pk;

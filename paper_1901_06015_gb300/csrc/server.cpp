@@ -264,7 +264,7 @@ void launch_wave(mxg_server_s* s, std::vector<Req*>& batch) {
     WaveBucket& b = wb[r->P.comp_double ? 1 : 0];
     GroupProb gp{};
     PackArgs ta{}, tb{};
-    group_describe_problem(r->P, s->arena_base + r->ws_off, &gp, &ta, &tb);
+    group_describe_problem(r->P, s->arena_base + r->ws_off, &gp, &ta, &tb, s->dev_err);
     b.probs.push_back(gp);
     for (const PackArgs& t : {ta, tb}) {
       b.tasks.push_back(t);

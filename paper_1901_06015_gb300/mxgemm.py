@@ -63,13 +63,16 @@ _GEMM_TAIL = [_i32, _i32, _i64, _i64, _i64, _dbl, _dbl, _vp, _i32, _i64, _i64,
 
 
 def lib():
-    """Load the CUDA library, building it in-tree first if it is missing or stale."""
+    """Load the CUDA library, building it in-tree first if it is missing or stale.
+    MXG_DEBUG_BOUNDS=1 in the environment loads (and builds) the bounds-checking debug
+    build instead."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if not _build.up_to_date():
-                path = _build.build()
+            debug = os.environ.get("MXG_DEBUG_BOUNDS", "") == "1"
+            path = _build.LIB_DEBUG if debug else _build.LIB
+            if not _build.up_to_date(debug):
+                path = _build.build(debug_bounds=debug)
             L = ctypes.CDLL(path)
             L.mxgemm.restype = _i32
             L.mxgemm.argtypes = _GEMM_TAIL
@@ -140,6 +143,7 @@ def lib():
             L.mxg_strerror.argtypes = [_i32]
             L.mxg_last_cuda_error.restype = _i32
             L.mxg_version.restype = _i32
+            L.mxg_debug_bounds.restype = _i32
             _lib = L
     return _lib
 
