@@ -45,7 +45,7 @@ constexpr int TC_BM = 128, TC_BN = 256, TC_GM = 16;
 constexpr uint32_t TILE_A = TC_BM * ROWB;                  // 8 KB
 constexpr uint32_t TILE_B = TC_BN * ROWB;                  // 16 KB
 constexpr uint32_t RING_BYTES = 192 * 1024;                // shared-memory ring
-constexpr uint32_t TC_SMEM = RING_BYTES + 1024 + 256;
+constexpr uint32_t TC_SMEM = RING_BYTES + 1024 + 256 + TC_STAGE_BYTES;   // ring, barriers, epilogue staging
 constexpr uint32_t TMEM_COLS = 2 * TC_BN;                  // two accumulators
 
 // Operand formats: the split forms load hi and lo planes of A and B and issue three
@@ -261,6 +261,9 @@ __device__ __forceinline__ void tc_body(const Src& src, int* err) {
   } else {
     // epilogue warps 2..5: TMEM lane quarter q = warp % 4
     const int q = warp & 3;
+    // this warp's staging buffers for old C values, after the barrier area
+    const uint32_t stage_w = bars + 256u + static_cast<uint32_t>(q) * TC_STAGE_WARP_BYTES;
+    const uint8_t* stage_w_gen = gen_base + (stage_w - base);
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const TcJob jb = src.job(t);
@@ -278,14 +281,7 @@ __device__ __forceinline__ void tc_body(const Src& src, int* err) {
       with_c_mode(jb.cdt, jb.mode, [&](auto C, auto M) {
         constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
         const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(e);
-#pragma unroll 1
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-          COld<CDT> old[TcChunk<MODE>::nold];
-          tc_epi_load<CDT, MODE>(e, row, n0 + c0, lane, old);
-          uint32_t v[32];
-          tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-          tc_epi_finish<CDT, MODE>(e, sc, row, n0 + c0, v, lane, old);
-        }
+        tc_epi_row<CDT, MODE, TC_BN>(e, sc, row, n0, tbase, lane, stage_w, stage_w_gen);
       });
       // release the accumulator to the MMA warp
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -46,7 +46,7 @@ constexpr int P_GM = 8;                           // pair rows per group of the 
 // GB300 at 8192^3: 1.25 PF/s with 64-byte rows, 1.66 PF/s with 128-byte rows).
 constexpr int P_RB = 128;
 constexpr uint32_t P_RING = 192 * 1024;
-constexpr uint32_t P_SMEM = P_RING + 1024 + 512;
+constexpr uint32_t P_SMEM = P_RING + 1024 + 512 + TC_STAGE_BYTES;   // ring, barriers, epilogue staging
 constexpr uint32_t P_TMEM_COLS = 2 * P_BN;        // two accumulators
 
 // RB: bytes of K per tile row (64 or 128, with the swizzle of that width).
@@ -296,6 +296,9 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
   } else {
     // epilogue warps 2..5: TMEM lane quarter q = warp % 4 of this CTA's 128 rows
     const int q = warp & 3;
+    // this warp's staging buffers for old C values, after the barrier area
+    const uint32_t stage_w = bars + 256u + static_cast<uint32_t>(q) * TC_STAGE_WARP_BYTES;
+    const uint8_t* stage_w_gen = gen_base + (stage_w - base);
     int j = 0;
     for (int t = cid; t < ntiles; t += ncl, ++j) {
       int pm, tn;
@@ -314,14 +317,7 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
       with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
         constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
         const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(g.e);
-#pragma unroll 1
-        for (int c0 = 0; c0 < P_BN; c0 += 32) {
-          COld<CDT> old[TcChunk<MODE>::nold];
-          tc_epi_load<CDT, MODE>(g.e, row, n0 + c0, lane, old);
-          uint32_t v[32];
-          tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-          tc_epi_finish<CDT, MODE>(g.e, sc, row, n0 + c0, v, lane, old);
-        }
+        tc_epi_row<CDT, MODE, P_BN>(g.e, sc, row, n0, tbase, lane, stage_w, stage_w_gen);
       });
       // release the accumulator to the even CTA's MMA thread
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
