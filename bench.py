@@ -461,7 +461,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_forms:
         del mats
         torch.cuda.empty_cache()
-        forms = {"grouped": grouped_form(args), "serving": serving_form(args)}
+        forms = {"plain_small": plain_small_form(args), "grouped": grouped_form(args), "serving": serving_form(args)}
 
     if rank == 0:
         line = {
@@ -482,6 +482,7 @@ def run_ours(args):
             line["grouped"]["kernels"] = [(b["precision"], b["kernel"], b["schedule"])
                                           for b in g["group"].get("buckets", [])]
             line["serving"] = sv
+            line["plain_small"] = forms["plain_small"]
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -570,6 +571,44 @@ def run_precision(args):
             "clocks": clocks, "results": results}
     print(json.dumps(line))
     return 0
+
+
+# ------------------------------------------------------------------ plain small form
+def plain_small_form(args, reps=20):
+    """The plain method on small problems: one mxgemm_ex call (AUTO: FFMA single, DFMA
+    double) for each of the 128 combinations at m = n = k = 128, column-major, no
+    transpose, U[-1, 1], alpha = 1.5, beta = -0.5 -- launch-latency bound. Per combo: the
+    mean of `reps` back-to-back calls (CUDA events around them on the stream)."""
+    import torch
+    import paper_1901_06015_gb300 as mx
+    from paper_1901_06015_gb300 import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    h = mx.Handle(); h.set_stream(stream)
+    gen = torch.Generator(device=dev); gen.manual_seed(0)
+    n = 128
+    per = {}
+    for combo in synth.all_combos():
+        A = synth.torch_matrix(gen, n, n, combo[1], dev)
+        B = synth.torch_matrix(gen, n, n, combo[2], dev)
+        C = synth.torch_matrix(gen, n, n, combo[0], dev)
+        for _ in range(3):
+            mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per[combo] = e0.elapsed_time(e1) / reps * 1e3            # microseconds per call
+    h.close()
+    us = sorted(per.values())
+    flops = {c: 2.0 * n ** 3 * real_products(c) for c in per}
+    return {"workload": "plain small: one call per combination, m=n=k=128, column-major, U[-1,1], alpha=1.5, "
+                        "beta=-0.5, method AUTO (FFMA single, DFMA double); mean of %d back-to-back calls" % reps,
+            "us_per_call_median": us[len(us) // 2], "us_per_call_min": us[0], "us_per_call_max": us[-1],
+            "gflops_all_combos": sum(flops.values()) / (sum(per.values()) / 1e6) / 1e9,
+            "per_combo_us": {c: round(v, 2) for c, v in per.items()}}
 
 
 # ------------------------------------------------------------------ grouped workload
@@ -867,8 +906,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="default workload: skip the grouped and serving forms that follow plain_large")
-    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision", "grouped", "serving", "single"])
+                    help="default workload: skip the plain-small, grouped and serving forms that follow plain_large")
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small", "precision", "grouped", "serving", "single"])
     ap.add_argument("--count", type=int, default=2048)
     ap.add_argument("--method-s", default="auto", choices=["auto", "ffma", "tf32x3", "bf16x3"],
                     help="grouped workload: method of the single-precision problems")
@@ -903,6 +942,13 @@ def main():
         return run_serving(args)
     if args.workload == "single":
         return run_single(args)
+    if args.workload == "plain_small":
+        r = plain_small_form(args)
+        print(json.dumps({"metric": METRIC, "workload": "plain_small", "value": r["gflops_all_combos"],
+                          "unit": "GFLOPS", "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32",
+                          "data": "synthetic", "config": {"workload": r["workload"]},
+                          **{k: v for k, v in r.items() if k != "workload"}}))
+        return 0
     return run_ours(args)
 
 
