@@ -587,26 +587,37 @@ def plain_small_form(args, reps=20):
     h = mx.Handle(); h.set_stream(stream)
     gen = torch.Generator(device=dev); gen.manual_seed(0)
     n = 128
-    per = {}
+    per, dev_us = {}, {}
     for combo in synth.all_combos():
         A = synth.torch_matrix(gen, n, n, combo[1], dev)
         B = synth.torch_matrix(gen, n, n, combo[2], dev)
         C = synth.torch_matrix(gen, n, n, combo[0], dev)
         for _ in range(3):
             mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
+        torch.cuda.synchronize()
+        h.set_phase_timing(True)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
             mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
         e1.record(stream)
         torch.cuda.synchronize()
+        pk, ct, nl = h.phase_times()
+        h.set_phase_timing(False)
         per[combo] = e0.elapsed_time(e1) / reps * 1e3            # microseconds per call
+        dev_us[combo] = (pk + ct) / max(nl, 1) * 1e3              # device time of the call's kernels
     h.close()
     us = sorted(per.values())
+    du = sorted(dev_us.values())
     flops = {c: 2.0 * n ** 3 * real_products(c) for c in per}
     return {"workload": "plain small: one call per combination, m=n=k=128, column-major, U[-1,1], alpha=1.5, "
                         "beta=-0.5, method AUTO (FFMA single, DFMA double); mean of %d back-to-back calls" % reps,
             "us_per_call_median": us[len(us) // 2], "us_per_call_min": us[0], "us_per_call_max": us[-1],
+            "device_us_per_call_median": du[len(du) // 2], "device_us_per_call_min": du[0],
+            "device_us_per_call_max": du[-1],
+            "timing": "us_per_call: CUDA events around 20 back-to-back calls from Python (host planning, the "
+                      "ctypes call and three launches); device_us: the call's pack and contraction kernels alone "
+                      "(the library's phase timing, events between its launches)",
             "gflops_all_combos": sum(flops.values()) / (sum(per.values()) / 1e6) / 1e9,
             "per_combo_us": {c: round(v, 2) for c, v in per.items()}}
 

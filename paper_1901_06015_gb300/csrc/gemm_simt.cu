@@ -345,7 +345,11 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
   const TileCfg t = tile_cfg(method);
   int64_t gx = g.Mp / t.tm, gy = g.Np / t.tn;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
-  if (method == MXG_METHOD_DFMA) {
+  // FFMA problems with fewer 128 x 128 tiles than half the SMs run 32 x 32 tiles instead
+  // (inside the same 128-padded packs): a small call spreads over up to 16x the CTAs,
+  // with the same per-element accumulation order, so the same results
+  const bool ffma_small = (method == MXG_METHOD_FFMA) && (gx * gy < 76);
+  if (method == MXG_METHOD_DFMA || ffma_small) {
     // DFMA runs 32 x 32 tiles over the real product's extent inside the 64-padded packs:
     // the FP64 pipe is busy with a few warps per SM, so smaller tiles only cut padding
     const int64_t mr = g.e.m * (mode == OUT_ROWPAIR ? 2 : 1), nr = g.e.n * (mode == OUT_COLPAIR ? 2 : 1);
@@ -359,7 +363,8 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
   if (method != MXG_METHOD_FFMA && method != MXG_METHOD_DFMA) return cudaErrorInvalidValue;
   const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto M) {
     constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
-    if (method == MXG_METHOD_FFMA) simt_gemm<float, 4, CDT, MODE><<<grid, 256, 0, s>>>(g);
+    if (method == MXG_METHOD_FFMA && ffma_small) simt_gemm<float, 1, CDT, MODE><<<grid, 256, 0, s>>>(g);
+    else if (method == MXG_METHOD_FFMA) simt_gemm<float, 4, CDT, MODE><<<grid, 256, 0, s>>>(g);
     else simt_gemm<double, 1, CDT, MODE><<<grid, 256, 0, s>>>(g);
   });
   return ok ? cudaGetLastError() : cudaErrorInvalidValue;
