@@ -125,20 +125,29 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[i][j] = T(0);
   const int tm = tid & 15, tn = tid >> 4;
+  // the next k-tile's source rows and the ring positions advance incrementally (no
+  // per-k-tile multiplications or modulo)
+  const T* Agn = Ag + static_cast<int64_t>(S - 1) * TK * lda;
+  const T* Bgn = Bg + static_cast<int64_t>(S - 1) * TK * ldb;
+  const int64_t a_step = static_cast<int64_t>(TK) * lda, b_step = static_cast<int64_t>(TK) * ldb;
+  const int64_t lda8 = 8 * lda, ldb8 = 8 * ldb;
+  int st_w = S - 1, st_r = 0;
   for (int64_t kt = 0; kt < nk; ++kt) {
     cp_async_wait<S - 2>();      // k-tile kt has landed (for this thread) ...
     __syncthreads();             // ... and for every thread; stage (kt-1) % S is free
-    const int64_t nxt = kt + S - 1;
-    if (nxt < nk) {
-      const int st = static_cast<int>(nxt % S);
+    if (kt + S - 1 < nk) {
 #pragma unroll
       for (int c = 0; c < CP; ++c) {
-        cp_async<VB>(&sm.As[st][lrow + 8 * c][lcol], Ag + (nxt * TK + 8 * c) * lda);
-        cp_async<VB>(&sm.Bs[st][lrow + 8 * c][lcol], Bg + (nxt * TK + 8 * c) * ldb);
+        cp_async<VB>(&sm.As[st_w][lrow + 8 * c][lcol], Agn + c * lda8);
+        cp_async<VB>(&sm.Bs[st_w][lrow + 8 * c][lcol], Bgn + c * ldb8);
       }
     }
     cp_async_commit();
-    const int buf = static_cast<int>(kt % S);
+    Agn += a_step;
+    Bgn += b_step;
+    const int buf = st_r;
+    st_w = (st_w + 1 == S) ? 0 : st_w + 1;
+    st_r = (st_r + 1 == S) ? 0 : st_r + 1;
     if (H == 1 && 4 * static_cast<int64_t>(tid >> 5) >= ncols) continue;   // whole warp in the padding
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
