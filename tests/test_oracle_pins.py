@@ -556,3 +556,27 @@ def test_identity_16bit_combos(combo):
     got = oracle_mxgemm("n", "n", alpha, A, B, -0.5 + 0.25j, C0.copy(), comp=x)
     scale = abs(alpha) * np.linalg.norm(Ah) * np.linalg.norm(Bh) + np.linalg.norm(C)
     assert np.linalg.norm(got - want) / scale < 1e-14
+
+
+def test_complex_beta_epilogue_rounding_exceeds_two_units():
+    """Pin of the tolerance's C-precision term for a complex beta: the epilogue's order of
+    operations in single precision (Sec. 7.1: beta*C as a naive complex product of four
+    rounded products and two rounded sums, then alpha*AB added with one more rounding)
+    can be 2.9 u away from the exact value in the normwise measure -- more than the 2 u of
+    a real beta, within the (1 + sqrt(5)) u of the Brent-Percival-Zimmermann bound for
+    the complex product plus the final rounding. Exact rational arithmetic, numpy float32
+    for the roundings."""
+    from fractions import Fraction as Fr
+    f = np.float32
+    br, bi = f(float.fromhex("-0x1.deb1eep-1")), f(float.fromhex("0x1.a777fep-1"))
+    cr, ci = f(float.fromhex("-0x1.122232p-1")), f(float.fromhex("-0x1.41cd64p-1"))
+    t = f(2.0 ** -24)
+    re = f(f(f(br * cr) - f(bi * ci)) + t)
+    im = f(f(br * ci) + f(bi * cr))
+    R = lambda x: Fr(float(x))
+    ex_re = R(br) * R(cr) - R(bi) * R(ci) + R(t)
+    ex_im = R(br) * R(ci) + R(bi) * R(cr)
+    num = float((R(re) - ex_re) ** 2 + (R(im) - ex_im) ** 2) ** 0.5
+    den = float((R(br) ** 2 + R(bi) ** 2) * (R(cr) ** 2 + R(ci) ** 2)) ** 0.5 + float(t)
+    u = 2.0 ** -24
+    assert 2.0 * u < num / den <= (1.0 + 5.0 ** 0.5) * u

@@ -297,3 +297,30 @@ def test_split_methods_below_their_smallest_k_are_rejected():
             assert np.array_equal(dC.cpu().numpy(), C0)
             A, B, C0 = synth.problem(31, combo, 40, 30, kmin)
             _check(combo, A, B, C0, 1.0, 1.0, method=meth)
+
+
+# beta, C and alpha*A*B of one element for which the epilogue's roundings in C's single
+# precision (Sec. 7.1: beta*C as a naive complex product, then the sum) cost 2.9 u_C in
+# the normwise measure: more than 2 u_C, within (1 + sqrt(5)) u_C
+EPI_WORST = dict(beta=complex(float.fromhex("-0x1.deb1eep-1"), float.fromhex("0x1.a777fep-1")),
+                 c=complex(float.fromhex("-0x1.122232p-1"), float.fromhex("-0x1.41cd64p-1")),
+                 t=2.0 ** -24)
+
+
+def test_complex_beta_epilogue_needs_more_than_two_roundings():
+    """The C-precision term for a complex beta is (1 + sqrt(5)) u_C, not 2 u_C: on this
+    element (case 1c, C complex single, double computation, k = 1) the kernel's result
+    is 2.9 u_C away from the exact value -- above 2 u_C, within (1 + sqrt(5)) u_C."""
+    from fractions import Fraction as Fr
+    b, c, t = EPI_WORST["beta"], EPI_WORST["c"], EPI_WORST["t"]
+    A = np.full((1, 1), t, dtype=np.float64, order="F")
+    B = np.ones((1, 1), dtype=np.float64, order="F")
+    C0 = np.full((1, 1), c, dtype=np.complex64, order="F")
+    got = complex(run("cddd", A, B, C0, 1.0, b, method="dfma")[0, 0])
+    exact_re = Fr(b.real) * Fr(c.real) - Fr(b.imag) * Fr(c.imag) + Fr(t)
+    exact_im = Fr(b.real) * Fr(c.imag) + Fr(b.imag) * Fr(c.real)
+    num = float((Fr(got.real) - exact_re) ** 2 + (Fr(got.imag) - exact_im) ** 2) ** 0.5
+    err = num / (t + abs(b) * abs(c))
+    u_c = 2.0 ** -24
+    assert 2.0 * u_c < err <= (1.0 + 5.0 ** 0.5) * u_c, err / u_c
+    assert err <= tolerance("cddd", 1, "dfma", b)
