@@ -602,17 +602,21 @@ def plain_small_form(args, reps=20):
         for _ in range(3):
             mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
         torch.cuda.synchronize()
-        h.set_phase_timing(True)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
             mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
         e1.record(stream)
         torch.cuda.synchronize()
+        per[combo] = e0.elapsed_time(e1) / reps * 1e3            # microseconds per call
+        # a second pass with the library's phase timing: the call's kernels alone (its
+        # events between the launches add a little)
+        h.set_phase_timing(True)
+        for _ in range(reps):
+            mx.mxgemm_ex(h, "auto", "n", "n", 1.5, A, B, -0.5, C, comp=combo[3])
         pk, ct, nl = h.phase_times()
         h.set_phase_timing(False)
-        per[combo] = e0.elapsed_time(e1) / reps * 1e3            # microseconds per call
-        dev_us[combo] = (pk + ct) / max(nl, 1) * 1e3              # device time of the call's kernels
+        dev_us[combo] = (pk + ct) / max(nl, 1) * 1e3
     h.close()
     us = sorted(per.values())
     du = sorted(dev_us.values())
@@ -623,8 +627,8 @@ def plain_small_form(args, reps=20):
             "device_us_per_call_median": du[len(du) // 2], "device_us_per_call_min": du[0],
             "device_us_per_call_max": du[-1],
             "timing": "us_per_call: CUDA events around 20 back-to-back calls from Python (host planning, the "
-                      "ctypes call and three launches); device_us: the call's pack and contraction kernels alone "
-                      "(the library's phase timing, events between its launches)",
+                      "ctypes call and three launches); device_us: a second pass of 20 calls with the library's "
+                      "phase timing (events before, between and after its launches)",
             "gflops_all_combos": sum(flops.values()) / (sum(per.values()) / 1e6) / 1e9,
             "per_combo_us": {c: round(v, 2) for c, v in per.items()}}
 
