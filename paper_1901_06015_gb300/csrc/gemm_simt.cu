@@ -170,12 +170,14 @@ __device__ __forceinline__ void simt_mainloop(const T* __restrict__ A, const T* 
   cp_async_wait<0>();
 }
 
-template <typename T, int H, int CDT, int MODE>
+// TW: threads per side of the tile's thread grid (16 x 16 threads; 8 x 8 for the 16 x 16
+// DFMA tiles).
+template <typename T, int H, int CDT, int MODE, int TW = 16>
 __device__ __forceinline__ void simt_epilogue(const EpiArgs& e, int64_t m0, int64_t n0, const T (&acc)[2 * H][2 * H]) {
   constexpr int R = 2 * H;
   constexpr int EB = (H == 1) ? 2 : H;   // C elements loaded together
   const EpiScalars<T, CDT> sc = epi_scalars<T, CDT>(e);
-  const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  const int tm = threadIdx.x % TW, tn = threadIdx.x / TW;
   auto row_of = [&](int i) -> int64_t { return m0 + frag_off<H>(tm, i); };
   auto col_of = [&](int j) -> int64_t { return n0 + frag_off<H>(tn, j); };
   // EB elements of one row (or row pair) of the thread's block at a time: their C
@@ -235,6 +237,67 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmA
   simt_mainloop<T, H>(static_cast<const T*>(g.A), static_cast<const T*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, sm, acc,
                       nreal - n0);
   simt_epilogue<T, H, CDT, MODE>(g.e, m0, n0, acc);
+}
+
+// DFMA on 16 x 16 tiles for double-precision calls too small to fill the device with
+// 32 x 32 tiles: 64 threads as 8 x 8, each the adjacent row pair 2t, 2t+1 and column
+// pair of the 32 x 32 kernel's mapping, k-tiles of 8 rows in a 4-stage cp.async ring
+// (one 16-byte copy per thread and operand). A problem gets 4x the CTAs, so 4x the SMs'
+// share of the FP64 pipe; each output is accumulated in increasing k as in every other
+// DFMA kernel, so the results are the same.
+constexpr int D16_TK = 8, D16_S = 4;
+
+template <int CDT, int MODE>
+__global__ void __launch_bounds__(64) dfma16_gemm(GemmArgs g) {
+  __shared__ __align__(16) double As[D16_S][D16_TK][16];
+  __shared__ __align__(16) double Bs[D16_S][D16_TK][16];
+  const int tid = threadIdx.x, tm = tid & 7, tn = tid >> 3;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 16, n0 = static_cast<int64_t>(blockIdx.y) * 16;
+  const double* A = static_cast<const double*>(g.A);
+  const double* B = static_cast<const double*>(g.B);
+  // copies: row tid / 8 of the k-tile, columns 2 * (tid % 8) .. +1 (one double2)
+  const int lrow = tid >> 3, lcol = (tid & 7) * 2;
+  const double* Ag = A + lrow * g.lda + m0 + lcol;
+  const double* Bg = B + lrow * g.ldb + n0 + lcol;
+  const int64_t nk = g.Kp / D16_TK;
+  const int64_t a_step = D16_TK * g.lda, b_step = D16_TK * g.ldb;
+#pragma unroll
+  for (int st = 0; st < D16_S - 1; ++st) {
+    if (st < nk) {
+      cp_async<16>(&As[st][lrow][lcol], Ag + st * a_step);
+      cp_async<16>(&Bs[st][lrow][lcol], Bg + st * b_step);
+    }
+    cp_async_commit();
+  }
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  const double* Agn = Ag + (D16_S - 1) * a_step;
+  const double* Bgn = Bg + (D16_S - 1) * b_step;
+  int st_w = D16_S - 1, st_r = 0;
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    cp_async_wait<D16_S - 2>();
+    __syncthreads();
+    if (kt + D16_S - 1 < nk) {
+      cp_async<16>(&As[st_w][lrow][lcol], Agn);
+      cp_async<16>(&Bs[st_w][lrow][lcol], Bgn);
+    }
+    cp_async_commit();
+    Agn += a_step;
+    Bgn += b_step;
+    const int buf = st_r;
+    st_w = (st_w + 1 == D16_S) ? 0 : st_w + 1;
+    st_r = (st_r + 1 == D16_S) ? 0 : st_r + 1;
+#pragma unroll
+    for (int kk = 0; kk < D16_TK; ++kk) {
+      const double2 a = *reinterpret_cast<const double2*>(&As[buf][kk][2 * tm]);
+      const double2 b = *reinterpret_cast<const double2*>(&Bs[buf][kk][2 * tn]);
+      acc[0][0] = fma(a.x, b.x, acc[0][0]);
+      acc[0][1] = fma(a.x, b.y, acc[0][1]);
+      acc[1][0] = fma(a.y, b.x, acc[1][0]);
+      acc[1][1] = fma(a.y, b.y, acc[1][1]);
+    }
+  }
+  cp_async_wait<0>();
+  simt_epilogue<double, 1, CDT, MODE, 8>(g.e, m0, n0, acc);
 }
 
 template <typename T, int H>
@@ -358,6 +421,7 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
   // (inside the same 128-padded packs): a small call spreads over up to 16x the CTAs,
   // with the same per-element accumulation order, so the same results
   const bool ffma_small = (method == MXG_METHOD_FFMA) && (gx * gy < 76);
+  bool dfma16 = false;
   if (method == MXG_METHOD_DFMA || ffma_small) {
     // DFMA runs 32 x 32 tiles over the real product's extent inside the 64-padded packs:
     // the FP64 pipe is busy with a few warps per SM, so smaller tiles only cut padding
@@ -365,6 +429,12 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
     gx = (mr + 31) / 32;
     gy = (nr + 31) / 32;
     if (gx <= 0 || gy <= 0) return cudaSuccess;
+    // and 16 x 16 tiles when 32 x 32 ones would leave more than half the SMs idle
+    if (method == MXG_METHOD_DFMA && gx * gy < 76) {
+      dfma16 = true;
+      gx = (mr + 15) / 16;
+      gy = (nr + 15) / 16;
+    }
   }
   if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
   const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
@@ -372,7 +442,8 @@ cudaError_t launch_gemm_simt(int method, int c_dt, int mode, const GemmArgs& g, 
   if (method != MXG_METHOD_FFMA && method != MXG_METHOD_DFMA) return cudaErrorInvalidValue;
   const bool ok = with_c_mode(c_dt, mode, [&](auto C, auto M) {
     constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
-    if (method == MXG_METHOD_FFMA && ffma_small) simt_gemm<float, 1, CDT, MODE><<<grid, 256, 0, s>>>(g);
+    if (dfma16) dfma16_gemm<CDT, MODE><<<grid, 64, 0, s>>>(g);
+    else if (method == MXG_METHOD_FFMA && ffma_small) simt_gemm<float, 1, CDT, MODE><<<grid, 256, 0, s>>>(g);
     else if (method == MXG_METHOD_FFMA) simt_gemm<float, 4, CDT, MODE><<<grid, 256, 0, s>>>(g);
     else simt_gemm<double, 1, CDT, MODE><<<grid, 256, 0, s>>>(g);
   });
