@@ -247,29 +247,31 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 3)) simt_gemm(GemmA
 // DFMA kernel, so the results are the same.
 constexpr int D16_TK = 8, D16_S = 4;
 
-template <int CDT, int MODE>
-__global__ void __launch_bounds__(64) dfma16_gemm(GemmArgs g) {
-  __shared__ __align__(16) double As[D16_S][D16_TK][16];
-  __shared__ __align__(16) double Bs[D16_S][D16_TK][16];
+struct D16Smem {
+  __align__(16) double As[D16_S][D16_TK][16];
+  __align__(16) double Bs[D16_S][D16_TK][16];
+};
+
+// Main loop of one 16 x 16 tile at (m0, n0); leaves the accumulators in acc.
+__device__ __forceinline__ void dfma16_mainloop(const double* __restrict__ A, const double* __restrict__ B,
+                                                int64_t lda, int64_t ldb, int64_t Kp, int64_t m0, int64_t n0,
+                                                D16Smem& sm, double (&acc)[2][2]) {
   const int tid = threadIdx.x, tm = tid & 7, tn = tid >> 3;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 16, n0 = static_cast<int64_t>(blockIdx.y) * 16;
-  const double* A = static_cast<const double*>(g.A);
-  const double* B = static_cast<const double*>(g.B);
   // copies: row tid / 8 of the k-tile, columns 2 * (tid % 8) .. +1 (one double2)
   const int lrow = tid >> 3, lcol = (tid & 7) * 2;
-  const double* Ag = A + lrow * g.lda + m0 + lcol;
-  const double* Bg = B + lrow * g.ldb + n0 + lcol;
-  const int64_t nk = g.Kp / D16_TK;
-  const int64_t a_step = D16_TK * g.lda, b_step = D16_TK * g.ldb;
+  const double* Ag = A + lrow * lda + m0 + lcol;
+  const double* Bg = B + lrow * ldb + n0 + lcol;
+  const int64_t nk = Kp / D16_TK;
+  const int64_t a_step = D16_TK * lda, b_step = D16_TK * ldb;
 #pragma unroll
   for (int st = 0; st < D16_S - 1; ++st) {
     if (st < nk) {
-      cp_async<16>(&As[st][lrow][lcol], Ag + st * a_step);
-      cp_async<16>(&Bs[st][lrow][lcol], Bg + st * b_step);
+      cp_async<16>(&sm.As[st][lrow][lcol], Ag + st * a_step);
+      cp_async<16>(&sm.Bs[st][lrow][lcol], Bg + st * b_step);
     }
     cp_async_commit();
   }
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = 0.0;
   const double* Agn = Ag + (D16_S - 1) * a_step;
   const double* Bgn = Bg + (D16_S - 1) * b_step;
   int st_w = D16_S - 1, st_r = 0;
@@ -277,8 +279,8 @@ __global__ void __launch_bounds__(64) dfma16_gemm(GemmArgs g) {
     cp_async_wait<D16_S - 2>();
     __syncthreads();
     if (kt + D16_S - 1 < nk) {
-      cp_async<16>(&As[st_w][lrow][lcol], Agn);
-      cp_async<16>(&Bs[st_w][lrow][lcol], Bgn);
+      cp_async<16>(&sm.As[st_w][lrow][lcol], Agn);
+      cp_async<16>(&sm.Bs[st_w][lrow][lcol], Bgn);
     }
     cp_async_commit();
     Agn += a_step;
@@ -288,16 +290,45 @@ __global__ void __launch_bounds__(64) dfma16_gemm(GemmArgs g) {
     st_r = (st_r + 1 == D16_S) ? 0 : st_r + 1;
 #pragma unroll
     for (int kk = 0; kk < D16_TK; ++kk) {
-      const double2 a = *reinterpret_cast<const double2*>(&As[buf][kk][2 * tm]);
-      const double2 b = *reinterpret_cast<const double2*>(&Bs[buf][kk][2 * tn]);
-      acc[0][0] = fma(a.x, b.x, acc[0][0]);
-      acc[0][1] = fma(a.x, b.y, acc[0][1]);
-      acc[1][0] = fma(a.y, b.x, acc[1][0]);
-      acc[1][1] = fma(a.y, b.y, acc[1][1]);
+      const double2 x = *reinterpret_cast<const double2*>(&sm.As[buf][kk][2 * tm]);
+      const double2 y = *reinterpret_cast<const double2*>(&sm.Bs[buf][kk][2 * tn]);
+      acc[0][0] = fma(x.x, y.x, acc[0][0]);
+      acc[0][1] = fma(x.x, y.y, acc[0][1]);
+      acc[1][0] = fma(x.y, y.x, acc[1][0]);
+      acc[1][1] = fma(x.y, y.y, acc[1][1]);
     }
   }
   cp_async_wait<0>();
+}
+
+template <int CDT, int MODE>
+__global__ void __launch_bounds__(64) dfma16_gemm(GemmArgs g) {
+  __shared__ D16Smem sm;
+  double acc[2][2];
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 16, n0 = static_cast<int64_t>(blockIdx.y) * 16;
+  dfma16_mainloop(static_cast<const double*>(g.A), static_cast<const double*>(g.B), g.lda, g.ldb, g.Kp, m0, n0, sm,
+                  acc);
   simt_epilogue<double, 1, CDT, MODE, 8>(g.e, m0, n0, acc);
+}
+
+// Grouped form: a persistent launch over a (problem, 16 x 16 tile) work list.
+__global__ void __launch_bounds__(64)
+dfma16_gemm_grouped(const GroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int ntiles,
+                    int* counter, int sched) {
+  __shared__ D16Smem sm;
+  __shared__ int slot;
+  double acc[2][2];
+  for (int t = next_tile(counter, &slot, -1, sched); t < ntiles; t = next_tile(counter, &slot, t, sched)) {
+    const GroupTile tl = tiles[t];
+    const GroupProb& p = probs[tl.prob];
+    const int64_t m0 = static_cast<int64_t>(tl.tm) * 16, n0 = static_cast<int64_t>(tl.tn) * 16;
+    __syncthreads();   // the previous tile's shared-memory reads are done
+    dfma16_mainloop(static_cast<const double*>(p.A), static_cast<const double*>(p.B), p.lda, p.ldb, p.Kp, m0, n0,
+                    sm, acc);
+    with_c_mode(p.cdt, p.mode, [&](auto C, auto M) {
+      simt_epilogue<double, 1, decltype(C)::value, decltype(M)::value, 8>(p.e, m0, n0, acc);
+    });
+  }
 }
 
 template <typename T, int H>
@@ -409,6 +440,7 @@ int variant_tile(int variant) {
     case VAR_DMMA_64: return 64;
     case VAR_DFMA_32: return 32;
     case VAR_FFMA_32: return 32;
+    case VAR_DFMA_16: return 16;
   }
   return 0;
 }
@@ -497,6 +529,7 @@ cudaError_t launch_gemm_grouped(int variant, const GroupProb* probs, const Group
     case VAR_DFMA_32: simt_gemm_grouped<double, 1><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_FFMA_32: simt_gemm_grouped<float, 1><<<grid, 256, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     case VAR_DMMA_64: return launch_dmma_grouped(probs, tiles, ntiles, counter, sched, grid, s);
+    case VAR_DFMA_16: dfma16_gemm_grouped<<<grid, 64, 0, s>>>(probs, tiles, ntiles, counter, sched); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -512,6 +545,7 @@ int grouped_blocks_per_sm(int variant) {
     case VAR_DFMA_32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<double, 1>, 256, 0); break;
     case VAR_FFMA_32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_gemm_grouped<float, 1>, 256, 0); break;
     case VAR_DMMA_64: return dmma_grouped_blocks_per_sm();
+    case VAR_DFMA_16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dfma16_gemm_grouped, 64, 0); break;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

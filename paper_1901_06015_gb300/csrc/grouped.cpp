@@ -405,7 +405,7 @@ int build_group(mxg_handle h, int64_t count, const mxg_problem* probs, int metho
   // chip); planning with the DFMA tile pads K' to 8 instead of the DMMA kernel's 16
   bd.plan_method = (method_d == MXG_METHOD_DMMA) ? MXG_METHOD_DMMA : MXG_METHOD_DFMA;
   bd.candidates = (method_d == MXG_METHOD_DMMA) ? std::vector<int>{VAR_DMMA_64}
-                                                : std::vector<int>{VAR_DFMA_32, VAR_DFMA_64};
+                                                : std::vector<int>{VAR_DFMA_32, VAR_DFMA_64, VAR_DFMA_16};
   const bool split_s = (method_s == MXG_METHOD_TF32X3 || method_s == MXG_METHOD_BF16X3);
   g->buckets[BK_S_TC].plan_method = method_s;
   g->buckets[BK_S_TC].tc_split = (method_s == MXG_METHOD_BF16X3) ? SPLIT_BF16 : SPLIT_TF32;
@@ -626,7 +626,8 @@ int mxg_group_run(mxg_group g) {
 
 int mxg_group_describe(mxg_group g, char* buf, size_t len) {
   if (!g || !buf || len == 0) return MXG_EINVAL;
-  static const char* vnames[VAR_COUNT] = {"ffma_128", "ffma_64", "dfma_64", "dfma_32", "dmma_64", "ffma_32"};
+  static const char* vnames[VAR_COUNT] = {"ffma_128", "ffma_64", "dfma_64", "dfma_32", "dmma_64", "ffma_32",
+                                          "dfma_16"};
   static const char* pnames[NBUCKETS] = {"s", "d", "s", "h", "b"};
   std::string s = "{\"problems\": " + std::to_string(g->plans.size()) + ", \"graph\": " +
                   (g->exec ? "true" : "false") + ", \"arena_bytes\": " + std::to_string(g->arena_bytes) +

@@ -16,9 +16,10 @@ enum GroupVariant : int {
   VAR_DFMA_64 = 2,    // FP64 DFMA, 64 x 64
   VAR_DFMA_32 = 3,    // FP64 DFMA, 32 x 32
   VAR_DMMA_64 = 4,    // FP64 DMMA, 64 x 64
-  VAR_FFMA_32 = 5     // FP32 FFMA, 32 x 32
+  VAR_FFMA_32 = 5,    // FP32 FFMA, 32 x 32
+  VAR_DFMA_16 = 6     // FP64 DFMA, 16 x 16 (64-thread CTAs)
 };
-constexpr int VAR_COUNT = 6;
+constexpr int VAR_COUNT = 7;
 
 // Tile schedules of the persistent kernels: DYNAMIC takes the next entry of the
 // (longest-first) work list from an atomic counter; STATIC gives CTA b the entries

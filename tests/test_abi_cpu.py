@@ -134,7 +134,7 @@ def test_empty_C_accepts_any_strides():
 
 def test_tune_file_round_trip(tmp_path):
     """The autotuner's decision file (host only, no CUDA call): mxg_tune_load keeps the
-    lines with a known kernel variant (0..5) and schedule (0 dynamic, 1 static) and drops
+    lines with a known kernel variant (0..6) and schedule (0 dynamic, 1 static) and drops
     the rest; mxg_tune_save writes back exactly what is held."""
     src = tmp_path / "in.txt"
     src.write_text("\n".join([

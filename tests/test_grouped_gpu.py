@@ -144,6 +144,7 @@ def test_one_shot_grouped_call():
     ("dmma", 4, "dmma"),   # DMMA 64 x 64
     ("dfma", 2, "dfma"),   # DFMA 64 x 64
     ("dfma", 3, "dfma"),   # DFMA 32 x 32 (adjacent row pairs per thread)
+    ("dfma", 6, "dfma"),   # DFMA 16 x 16 (64-thread CTAs)
 ])
 @pytest.mark.parametrize("variant_s", [0, 1, 5])   # FFMA 128, 64, 32
 def test_every_grouped_kernel_equals_solo(tmp_path, method_d, variant, solo_d, variant_s):
@@ -164,7 +165,7 @@ def test_every_grouped_kernel_equals_solo(tmp_path, method_d, variant, solo_d, v
     items, dev = _device_items(probs)
     g = mx.Group(items, method_d=method_d, tune=False, graph=True)
     kernels = {b["precision"]: b["kernel"] for b in g.describe()["buckets"]}
-    names = {0: "ffma_128", 1: "ffma_64", 5: "ffma_32", 2: "dfma_64", 3: "dfma_32", 4: "dmma_64"}
+    names = {0: "ffma_128", 1: "ffma_64", 5: "ffma_32", 2: "dfma_64", 3: "dfma_32", 4: "dmma_64", 6: "dfma_16"}
     assert kernels.get("s", names[variant_s]) == names[variant_s]
     assert kernels.get("d", names[variant]) == names[variant]
     g.run()
