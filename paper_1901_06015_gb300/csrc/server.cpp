@@ -275,7 +275,10 @@ void launch_wave(mxg_server_s* s, std::vector<Req*>& batch) {
   for (WaveBucket& b : wb) {
     if (b.probs.empty()) continue;
     if (b.comp_double) {
-      b.variant = (s->method_d == MXG_METHOD_DMMA) ? VAR_DMMA_64 : VAR_DFMA_32;
+      // DFMA on 32 x 32 tiles once they fill the device, else 16 x 16 for more CTAs
+      const size_t t32 = group_tiles(b.probs, VAR_DFMA_32).size();
+      b.variant = (s->method_d == MXG_METHOD_DMMA) ? VAR_DMMA_64
+                  : (t32 >= static_cast<size_t>(2 * s->sm_count)) ? VAR_DFMA_32 : VAR_DFMA_16;
     } else {
       // 64 x 64 tiles once they fill the device, else 32 x 32 for more CTAs
       const size_t t64 = group_tiles(b.probs, VAR_FFMA_64).size();
