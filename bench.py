@@ -883,6 +883,7 @@ def run_single(args):
     h = mx.Handle(); h.set_stream(stream)
     h.set_split_k(args.split_k)
     h.set_cta_pairs(args.cta_pairs)
+    h.set_stream_k(args.stream_k)
     R = real_products(combo)
     times = []
     h.set_phase_timing(True)
@@ -907,7 +908,7 @@ def run_single(args):
     c_bytes = 2.0 * mm * nn * C.element_size() * (2 if C.dim() == 3 else 1)
     c_ms = (con_ms / nl) if nl else min(times)
     line = {"workload": "single", "combo": combo, "method": args.method, "m_n_k": [mm, nn, kk], "reps": args.reps,
-            "split_k": args.split_k, "cta_pairs": args.cta_pairs,
+            "split_k": args.split_k, "cta_pairs": args.cta_pairs, "stream_k": args.stream_k,
             "layout": [la, lb, lc], "trans": [args.transa, args.transb],
             "best_ms": min(times), "gflops": fl / min(times) / 1e6,
             "contraction_ms_mean": con_ms / max(nl, 1), "pack_ms_mean": pack_ms / max(nl, 1),
@@ -941,6 +942,8 @@ def main():
     ap.add_argument("--mnk", default="", help="m,n,k for --workload single (default: --size cubed)")
     ap.add_argument("--split-k", type=int, default=0)
     ap.add_argument("--cta-pairs", type=int, default=0, help="tensor-core methods: 0 auto, 1 pairs, 2 single CTAs")
+    ap.add_argument("--stream-k", type=int, default=1,
+                    help="stream-K tail of the CTA-pair kernel: 0 off, 1 auto, 2 whenever the last wave is partial")
     ap.add_argument("--requests", type=int, default=100000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--streams", type=int, default=4)

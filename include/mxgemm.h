@@ -211,10 +211,24 @@ int mxg_set_split_k(mxg_handle h, int mode);
  * (= pairs), 1 pairs, 2 one CTA per tile. A pair is a cluster of two CTAs on two SMs
  * computing a 256 x 256 tile with tcgen05 cta_group::2 MMAs; each CTA loads its own
  * half of the tile's A and B rows (128-byte k rows), so the operands cost a third fewer
- * bytes, and half the requests, from L2 per flop than single-CTA 128 x 256 tiles. The
- * two kernels give the same results bit for bit (tested; same products, accumulated in
- * the same order along k). */
+ * bytes, and half the requests, from L2 per flop than single-CTA 128 x 256 tiles. With
+ * the stream-K tail off (mxg_set_stream_k mode 0) the two kernels give the same results
+ * bit for bit (tested; same products, accumulated in the same order along k). */
 int mxg_set_cta_pairs(mxg_handle h, int mode);
+
+/* Stream-K tail of the CTA-pair kernel on h: mode 0 off, 1 automatic (the default), 2
+ * whenever the last wave of pair tiles is partial. With T pair tiles on P resident pairs
+ * and r = T mod P > 0, the last r tiles are cut along k into P equal ranges, one per
+ * pair, so no pair idles through a partial last wave. Each range's FP32 partial
+ * accumulator goes to the workspace; the range that finishes a tile last adds the
+ * tile's partials in increasing k and applies the epilogue (Sec. 7.1) to the sum, so
+ * the result is the same from run to run. It differs from a whole-tile run only in the
+ * FP32 summation order along k; the stated bound holds for both. Automatic mode runs
+ * the tail when the last wave is at most 4/5 full and each range has at least 8 k
+ * blocks. The tail adds (SMs / 2) x 512 KB (+ counters) to the workspace; a caller
+ * workspace that holds the rest of the plan but not this runs without the tail.
+ * mxgemm_noalloc and the server never use it. */
+int mxg_set_stream_k(mxg_handle h, int mode);
 
 /* Stream for subsequent calls on h (a cudaStream_t; NULL = legacy default stream). */
 int mxg_set_stream(mxg_handle h, void* stream);

@@ -219,7 +219,12 @@ int make_plan(const Call& c, int method, Plan* p) {
       P.bytes_ws = align256(static_cast<size_t>(P.splits) * P.Mp * P.Np * esz_of(P));
     }
   }
-  P.workspace = P.bytes_a + P.bytes_b + P.bytes_ws;
+  // Stream-K tail of the pair kernel: partial accumulators and tile counters.
+  if (P.pairs && c.stream_k) {
+    P.stream_k = c.stream_k;
+    P.bytes_sk = tc_pair_stream_k_workspace(P.split, P.Mp, P.Np, P.Kp, c.sm_count, c.stream_k);
+  }
+  P.workspace = P.bytes_a + P.bytes_b + P.bytes_ws + P.bytes_sk;
   return MXG_OK;
 }
 
@@ -287,7 +292,9 @@ int enqueue_plan(const Plan& P, void* ws, cudaStream_t s, cudaEvent_t ev_mid, in
     const void* planes[4] = {base, one ? base : base + P.plane_a, base + P.bytes_a,
                              one ? base + P.bytes_a : base + P.bytes_a + P.plane_b};
     const cudaError_t e =
-        P.pairs ? launch_gemm_tc_pair(P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, ep, dev_err, s)
+        P.pairs ? launch_gemm_tc_pair(P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, ep, dev_err,
+                                      P.bytes_sk ? base + P.bytes_a + P.bytes_b + P.bytes_ws : nullptr,
+                                      P.bytes_sk, P.stream_k, s)
                 : launch_gemm_tc(P.method, P.split, w.dtC, P.mode, planes, P.Mp, P.Np, P.Kp, ep, dev_err,
                                  s);
     return e == cudaErrorNotSupported ? MXG_ENOTSUP : cuda_status(e);
@@ -389,6 +396,7 @@ int mxg_plan(int method, int transa, int transb, int64_t m, int64_t n, int64_t k
   c.alpha_re = alpha_re; c.alpha_im = alpha_im; c.beta_re = 1.0; c.beta_im = 0.0;
   c.dtA = dtA; c.rsA = rsA; c.csA = csA; c.dtB = dtB; c.rsB = rsB; c.csB = csB;
   c.dtC = dtC; c.rsC = rsC; c.csC = csC; c.comp = comp_prec;
+  c.stream_k = 1;   // a handle's default
   Plan P;
   const int st = make_plan(c, method, &P);
   if (st != MXG_OK) return st;
@@ -445,6 +453,13 @@ int mxg_set_cta_pairs(mxg_handle h, int mode) {
   if (!h || mode < 0 || mode > 2) return MXG_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
   h->cta_pairs = mode;
+  return MXG_OK;
+}
+
+int mxg_set_stream_k(mxg_handle h, int mode) {
+  if (!h || mode < 0 || mode > 2) return MXG_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->stream_k = mode;
   return MXG_OK;
 }
 
@@ -554,6 +569,7 @@ int mxgemm_ex(mxg_handle h, int method, int transa, int transb, int64_t m, int64
   c.split_k = h->split_k;
   c.sm_count = h->sm_count;
   c.cta_pairs = h->cta_pairs;
+  c.stream_k = h->stream_k;
   Plan P;
   int st = make_plan(c, method, &P);
   if (st != MXG_OK) return st;
@@ -561,6 +577,11 @@ int mxgemm_ex(mxg_handle h, int method, int transa, int transb, int64_t m, int64
   if (!C) return MXG_EINVAL;
   if (P.kind == PLAN_GEMM && (!A || !B)) return MXG_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
+  // a caller workspace that holds everything but the stream-K tail runs without the tail
+  if (!h->ws_owned && P.bytes_sk && P.workspace > h->ws_bytes && P.workspace - P.bytes_sk <= h->ws_bytes) {
+    P.workspace -= P.bytes_sk;
+    P.bytes_sk = 0;
+  }
   void* ws = nullptr;
   st = ensure_workspace(h, P.kind == PLAN_GEMM ? P.workspace : 0, &ws);
   if (st != MXG_OK) return st;

@@ -17,6 +17,7 @@ struct mxg_context {
   bool literal_alpha = false;
   int split_k = 0;
   int cta_pairs = 0;
+  int stream_k = 1;
   int sm_count = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<cudaEvent_t> ev_rec;   // triples: before packs, before contraction, after

@@ -27,6 +27,17 @@
 // abort flags, skips its stores, drains its own MMAs and copies (bounded), and the pair
 // meets at a final cluster barrier before freeing tensor memory, so neither CTA exits
 // while the other may still touch its shared or tensor memory.
+//
+// Stream-K tail. When the pair tiles do not fill a whole number of waves (T tiles on P
+// resident pairs, r = T mod P > 0), the last r tiles of the order are cut along k into P
+// equal ranges of the r * nkb (tile, k-block) steps, one per pair, processed before the
+// pair's whole tiles: every pair then does the same work, instead of r pairs running a
+// last wave alone. A range covers the ends of at most two tiles. Its epilogue writes the
+// FP32 partial accumulator to the workspace (one slot per pair, range part and CTA) and
+// takes a ticket on the tile's counter; the warp that takes the last ticket adds the
+// tile's partials in increasing k (a fixed order, so the result does not depend on which
+// pair finished last) and applies the epilogue of Sec. 7.1 to the sum. Nothing waits on
+// another pair: the ticket replaces the wait.
 #include <algorithm>
 
 #include "tc_common.cuh"
@@ -67,7 +78,56 @@ struct PairArgs {
   EpiArgs e;
   int cdt, mode;
   int* err;
+  // stream-K tail (sk_r > 0): tiles [sk_full * P, sk_full * P + sk_r) of the order are
+  // cut along k; sk_part holds 4 slots of P_BM x P_BN FP32 per pair, sk_cnt 8 counters
+  // per tail tile (CTA, epilogue warp), zero at launch
+  float4* sk_part;
+  int* sk_cnt;
+  int sk_full, sk_r;
 };
+
+// One item of a pair's work: tile t (index in the order), k-blocks [kb0, kb1); for a
+// range of a stream-K tile, tl is the tile's index in the tail and seg the range's part
+// (0 or 1) in this pair's slots, else tl = -1.
+struct PairItem {
+  int t, kb0, kb1, tl, seg;
+};
+
+// First k-block step of pair c's range: c * W / P of the W tail steps.
+__device__ __forceinline__ int64_t sk_begin(int64_t W, int P, int c) { return W * c / P; }
+// The pair whose range holds tail step x: the largest c with sk_begin(c) <= x.
+__device__ __forceinline__ int sk_owner(int64_t W, int P, int64_t x) {
+  return static_cast<int>(((x + 1) * P + W - 1) / W) - 1;
+}
+
+// Item i of pair cid (ncl pairs): its stream-K ranges first, then its whole tiles.
+__device__ __forceinline__ bool pair_item(const PairArgs& g, int ntiles, int nkb, int cid, int ncl, int i,
+                                          PairItem* w) {
+  if (g.sk_r == 0) {
+    const int t = cid + i * ncl;
+    if (t >= ntiles) return false;
+    *w = PairItem{t, 0, nkb, -1, -1};
+    return true;
+  }
+  const int64_t W = static_cast<int64_t>(g.sk_r) * nkb;
+  const int64_t kb = sk_begin(W, ncl, cid), ke = sk_begin(W, ncl, cid + 1);
+  int nseg = 0, tl0 = 0;
+  if (ke > kb) {
+    tl0 = static_cast<int>(kb / nkb);
+    nseg = static_cast<int>((ke - 1) / nkb) - tl0 + 1;
+  }
+  if (i < nseg) {
+    const int tl = tl0 + i;
+    const int64_t t0 = static_cast<int64_t>(tl) * nkb;
+    const int lo = static_cast<int>(max(kb, t0) - t0), hi = static_cast<int>(min(ke, t0 + nkb) - t0);
+    *w = PairItem{g.sk_full * ncl + tl, lo, hi, tl, i};
+    return true;
+  }
+  const int t = cid + (i - nseg) * ncl;
+  if (t >= g.sk_full * ncl) return false;
+  *w = PairItem{t, 0, nkb, -1, -1};
+  return true;
+}
 
 __device__ __forceinline__ uint32_t cta_rank() {
   uint32_t r;
@@ -159,6 +219,66 @@ __device__ __forceinline__ void pair_coords(int t, int pairs_m, int tiles_n, int
   *tn = r / gsz;
 }
 
+// float4 index of the slot of pair c, range part seg, CTA rank: P_BM x P_BN FP32 as
+// [column / 4][row][4], so a warp's 32 rows of four columns are 512 contiguous bytes.
+constexpr int SK_SLOT4 = P_BM * P_BN / 4;
+// Bytes of the partial slots for `pairs` pairs (two range parts, two CTAs each).
+constexpr size_t sk_part_bytes(int64_t pairs) { return static_cast<size_t>(pairs) * 4 * SK_SLOT4 * 16; }
+__device__ __forceinline__ int64_t sk_slot(int c, int seg, uint32_t rank) {
+  return ((static_cast<int64_t>(c) * 2 + seg) * 2 + rank) * SK_SLOT4;
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+      ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+        "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+        "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+// The sum of a stream-K tile's partial accumulators for this thread's row (the ranges
+// of pairs c_first .. c_last, in increasing k), written over the accumulator in tensor
+// memory (tbase), where the tile's ordinary epilogue then reads it.
+__device__ __forceinline__ void sk_sum_to_tmem(const PairArgs& g, uint32_t tbase, int rl, uint32_t rank, int tl,
+                                               int nkb, int ncl, int c_first, int c_last) {
+  const int64_t W = static_cast<int64_t>(g.sk_r) * nkb;
+#pragma unroll 1
+  for (int c0 = 0; c0 < P_BN; c0 += 32) {
+    float a[32];
+#pragma unroll 1
+    for (int c = c_first; c <= c_last; ++c) {
+      const int seg = tl - static_cast<int>(sk_begin(W, ncl, c) / nkb);
+      const float4* slot = g.sk_part + sk_slot(c, seg, rank) + rl + (c0 >> 2) * P_BM;
+      float4 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = __ldcg(slot + u * P_BM);
+      if (c == c_first) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a[4 * u] = x[u].x; a[4 * u + 1] = x[u].y; a[4 * u + 2] = x[u].z; a[4 * u + 3] = x[u].w;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a[4 * u] = __fadd_rn(a[4 * u], x[u].x);
+          a[4 * u + 1] = __fadd_rn(a[4 * u + 1], x[u].y);
+          a[4 * u + 2] = __fadd_rn(a[4 * u + 2], x[u].z);
+          a[4 * u + 3] = __fadd_rn(a[4 * u + 3], x[u].w);
+        }
+      }
+    }
+    uint32_t v[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) v[jj] = __float_as_uint(a[jj]);
+    tmem_st32(tbase + static_cast<uint32_t>(c0), v);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 template <int SPLIT, int RB>
 __global__ void __launch_bounds__(192, 1)
 tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
@@ -226,12 +346,13 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int t = cid; t < ntiles && ok; t += ncl) {
+      PairItem w;
+      for (int i = 0; ok && pair_item(g, ntiles, nkb, cid, ncl, i, &w); ++i) {
         int pm, tn;
-        pair_coords(t, pairs_m, tiles_n, &pm, &tn);
+        pair_coords(w.t, pairs_m, tiles_n, &pm, &tn);
         const int32_t ym = pm * 2 * P_BM + static_cast<int32_t>(rank) * P_BM;
         const int32_t yn = tn * P_BN + static_cast<int32_t>(rank) * (P_BN / 2);
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
+        for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
           const int s = static_cast<int>(it % S);
           const uint32_t use = it / S;
           if (!mbar_wait_cl(empty(s), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -259,13 +380,13 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
     if (lane == 0 && leader) {
       uint32_t it = 0;
       bool ok = true;
-      int j = 0;
-      for (int t = cid; t < ntiles && ok; t += ncl, ++j) {
+      PairItem w;
+      for (int j = 0; ok && pair_item(g, ntiles, nkb, cid, ncl, j, &w); ++j) {
         const int b = j & 1;
         if (!mbar_wait_cl(acc_empty(b), (static_cast<uint32_t>(j >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_tmem = tmem + static_cast<uint32_t>(b * P_BN);
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
+        for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
           const int s = static_cast<int>(it % S);
           if (!mbar_wait_cl(full(s), (it / S) & 1u, abort_flag)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -274,7 +395,7 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
 #pragma unroll
           for (int kk = 0; kk < KSTEPS; ++kk) {
             const uint32_t off = kk * 32;
-            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            const uint32_t first = (kb == w.kb0 && kk == 0) ? 0u : 1u;
             mma_pair<SPLIT>(acc_tmem, swz_desc<RB>(a_hi + off), swz_desc<RB>(b_hi + off), first);
             if constexpr (F::planes == 2) {
               mma_pair<SPLIT>(acc_tmem, swz_desc<RB>(a_hi + off), swz_desc<RB>(b_lo + off), 1u);
@@ -299,10 +420,19 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
     // this warp's staging buffers for old C values, after the barrier area
     const uint32_t stage_w = bars + 256u + static_cast<uint32_t>(q) * TC_STAGE_WARP_BYTES;
     const uint8_t* stage_w_gen = gen_base + (stage_w - base);
-    int j = 0;
-    for (int t = cid; t < ntiles; t += ncl, ++j) {
+    const int rl = 32 * q + lane;   // this thread's row of the CTA's 128
+    auto release = [&](int b) {       // hand the accumulator back to the even CTA's MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (leader) mbar_arrive(acc_empty(b));
+        else mbar_arrive_cluster(peer_addr(acc_empty(b), 0));
+      }
+    };
+    PairItem w;
+    for (int j = 0; pair_item(g, ntiles, nkb, cid, ncl, j, &w); ++j) {
       int pm, tn;
-      pair_coords(t, pairs_m, tiles_n, &pm, &tn);
+      pair_coords(w.t, pairs_m, tiles_n, &pm, &tn);
       const int b = j & 1;
       const bool ok = mbar_wait_cl(acc_full(b), static_cast<uint32_t>(j >> 1) & 1u, abort_flag);
       if (!__all_sync(0xffffffffu, ok && !*abort_flag)) {
@@ -312,20 +442,45 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t m0 = static_cast<int64_t>(pm) * 2 * P_BM + static_cast<int64_t>(rank) * P_BM;
       const int64_t n0 = static_cast<int64_t>(tn) * P_BN;
-      const int64_t row = m0 + 32 * q + lane;
+      const int64_t row = m0 + rl;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b * P_BN);
+      if (w.tl >= 0) {
+        // a range of a stream-K tile: its partial accumulator to this pair's slot
+        float4* slot = g.sk_part + sk_slot(cid, w.seg, rank) + rl;
+#pragma unroll 1
+        for (int c0 = 0; c0 < P_BN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            __stcg(slot + ((c0 >> 2) + u) * P_BM,
+                   make_float4(__uint_as_float(v[4 * u]), __uint_as_float(v[4 * u + 1]),
+                               __uint_as_float(v[4 * u + 2]), __uint_as_float(v[4 * u + 3])));
+        }
+        // a ticket on the tile's counter for this CTA and warp: the last of the tile's
+        // ranges sums them all into its accumulator and runs the epilogue
+        const int64_t W = static_cast<int64_t>(g.sk_r) * nkb;
+        const int c_first = sk_owner(W, ncl, static_cast<int64_t>(w.tl) * nkb);
+        const int c_last = sk_owner(W, ncl, static_cast<int64_t>(w.tl + 1) * nkb - 1);
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0)
+          last = (atomicAdd(g.sk_cnt + (w.tl * 2 + static_cast<int>(rank)) * 4 + q, 1) == c_last - c_first);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) {
+          release(b);
+          continue;
+        }
+        __threadfence();
+        sk_sum_to_tmem(g, tbase, rl, rank, w.tl, nkb, ncl, c_first, c_last);
+      }
       with_c_mode(g.cdt, g.mode, [&](auto C, auto M) {
         constexpr int CDT = decltype(C)::value, MODE = decltype(M)::value;
         const EpiScalars<float, CDT> sc = epi_scalars<float, CDT>(g.e);
         tc_epi_row<CDT, MODE, P_BN>(g.e, sc, row, n0, tbase, lane, stage_w, stage_w_gen);
       });
-      // release the accumulator to the even CTA's MMA thread
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        if (leader) mbar_arrive(acc_empty(b));
-        else mbar_arrive_cluster(peer_addr(acc_empty(b), 0));
-      }
+      release(b);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -339,11 +494,13 @@ tc_pair_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CU
 }
 
 template <int SPLIT, int RB>
-cudaError_t launch_pair(const CUtensorMap* maps, const PairArgs& g, int sms, cudaStream_t s) {
+cudaError_t launch_pair(const CUtensorMap* maps, PairArgs g, int sms, void* sk_ws, size_t sk_bytes, int sk_mode,
+                        cudaStream_t s) {
   auto kern = tc_pair_gemm<SPLIT, RB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM);
   if (e != cudaSuccess) return e;
   const int64_t npairs = ((g.Mp + 2 * P_BM - 1) / (2 * P_BM)) * (g.Np / P_BN);
+  const int64_t nkb = g.Kp * PairFmt<SPLIT, RB>::elem / RB;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -362,7 +519,18 @@ cudaError_t launch_pair(const CUtensorMap* maps, const PairArgs& g, int sms, cud
     cudaGetLastError();
     max_clusters = sms / 2;
   }
-  const int64_t ncl = std::min<int64_t>(npairs, std::min(max_clusters, sms / 2));
+  const int64_t resident = std::min(max_clusters, sms / 2);
+  int64_t ncl = std::min<int64_t>(npairs, resident);
+  g.sk_part = nullptr; g.sk_cnt = nullptr; g.sk_full = 0; g.sk_r = 0;
+  if (sk_ws && tc_pair_stream_k(npairs, nkb, resident, sk_mode) && tc_pair_stream_k_bytes(resident) <= sk_bytes) {
+    ncl = resident;
+    g.sk_full = static_cast<int>(npairs / ncl);
+    g.sk_r = static_cast<int>(npairs % ncl);
+    g.sk_part = static_cast<float4*>(sk_ws);
+    g.sk_cnt = reinterpret_cast<int*>(static_cast<char*>(sk_ws) + sk_part_bytes(resident));
+    e = cudaMemsetAsync(g.sk_cnt, 0, static_cast<size_t>(g.sk_r) * 8 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   if (ncl <= 0) return cudaErrorInvalidValue;
   cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl), 1, 1);
   e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], g);
@@ -371,10 +539,33 @@ cudaError_t launch_pair(const CUtensorMap* maps, const PairArgs& g, int sms, cud
 
 }  // namespace
 
+bool tc_pair_stream_k(int64_t tiles, int64_t nkb, int64_t pairs, int mode) {
+  if (mode <= 0 || tiles <= 0 || nkb <= 0 || pairs <= 0) return false;
+  const int64_t r = tiles % pairs;
+  // every pair's range must hold at least one k-block (a tile's ranges are then the
+  // consecutive pairs c_first .. c_last, each taking one ticket)
+  if (r == 0 || r * nkb < pairs) return false;
+  if (mode >= 2) return true;
+  // automatic: the last wave at most 4/5 full, and at least 8 k-blocks per range
+  return 5 * r <= 4 * pairs && r * nkb >= 8 * pairs;
+}
+
+size_t tc_pair_stream_k_bytes(int64_t pairs) {
+  return pairs <= 0 ? 0 : sk_part_bytes(pairs) + ((static_cast<size_t>(pairs) * 8 * sizeof(int) + 255) & ~size_t(255));
+}
+
+size_t tc_pair_stream_k_workspace(int split, int64_t Mp, int64_t Np, int64_t Kp, int sm_count, int mode) {
+  const int64_t elem = (split == SPLIT_TF32) ? 4 : 2;
+  const int64_t pairs = (sm_count > 0 ? sm_count : 152) / 2;
+  const int64_t tiles = ((Mp + 2 * P_BM - 1) / (2 * P_BM)) * (Np / P_BN);
+  return tc_pair_stream_k(tiles, Kp * elem / P_RB, pairs, mode) ? tc_pair_stream_k_bytes(pairs) : 0;
+}
+
 // planes: A_hi, A_lo (Mp x Kp, K-major), B_hi, B_lo (Np x Kp, K-major); one plane per
 // operand for the one-pass formats (the lo entries are ignored)
 cudaError_t launch_gemm_tc_pair(int split, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,
-                                int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s) {
+                                int64_t Kp, const EpiArgs& e, int* err, void* sk_ws, size_t sk_bytes, int sk_mode,
+                                cudaStream_t s) {
   if (!tc_get_encoder()) return cudaErrorNotSupported;
   const int elem = (split == SPLIT_TF32) ? 4 : 2;
   if (Mp % P_BM || Np % P_BN || (Kp * elem) % P_RB) return cudaErrorInvalidValue;
@@ -390,15 +581,15 @@ cudaError_t launch_gemm_tc_pair(int split, int c_dt, int mode, const void* const
       !tc_make_map(&maps[2], planes[2], split, Np, Kp, P_BN / 2, P_RB) ||
       !tc_make_map(&maps[3], planes[3], split, Np, Kp, P_BN / 2, P_RB))
     return cudaErrorInvalidValue;
-  PairArgs g{Mp, Np, Kp, e, c_dt, mode, err};
+  PairArgs g{Mp, Np, Kp, e, c_dt, mode, err, nullptr, nullptr, 0, 0};
   bool valid = false;
   with_c_mode(c_dt, mode, [&](auto, auto) { valid = true; });
   if (!valid) return cudaErrorInvalidValue;
   switch (split) {
-    case SPLIT_TF32: return launch_pair<SPLIT_TF32, P_RB>(maps, g, sms, s);
-    case SPLIT_BF16: return launch_pair<SPLIT_BF16, P_RB>(maps, g, sms, s);
-    case SPLIT_F16_ONE: return launch_pair<SPLIT_F16_ONE, P_RB>(maps, g, sms, s);
-    case SPLIT_BF16_ONE: return launch_pair<SPLIT_BF16_ONE, P_RB>(maps, g, sms, s);
+    case SPLIT_TF32: return launch_pair<SPLIT_TF32, P_RB>(maps, g, sms, sk_ws, sk_bytes, sk_mode, s);
+    case SPLIT_BF16: return launch_pair<SPLIT_BF16, P_RB>(maps, g, sms, sk_ws, sk_bytes, sk_mode, s);
+    case SPLIT_F16_ONE: return launch_pair<SPLIT_F16_ONE, P_RB>(maps, g, sms, sk_ws, sk_bytes, sk_mode, s);
+    case SPLIT_BF16_ONE: return launch_pair<SPLIT_BF16_ONE, P_RB>(maps, g, sms, sk_ws, sk_bytes, sk_mode, s);
   }
   return cudaErrorInvalidValue;
 }

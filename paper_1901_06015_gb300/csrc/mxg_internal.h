@@ -120,8 +120,18 @@ cudaError_t launch_wait_timeout_probe(int* err, double seconds, cudaStream_t s);
 cudaError_t launch_gemm_tc(int method, int split, int c_dt, int mode, const void* const planes[4], int64_t Mp,
                            int64_t Np, int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s);
 // The same contraction on CTA pairs (tcgen05 cta_group::2, 256 x 256 pair tiles; Mp a
-// multiple of 128, Np of 256).
+// multiple of 128, Np of 256). sk_ws / sk_bytes: workspace for the stream-K tail (null:
+// none); sk_mode 0 off, 1 automatic, 2 whenever the last wave is partial. The tail runs
+// only when the workspace holds tc_pair_stream_k_bytes(resident pairs).
 cudaError_t launch_gemm_tc_pair(int split, int c_dt, int mode, const void* const planes[4], int64_t Mp, int64_t Np,
-                                int64_t Kp, const EpiArgs& e, int* err, cudaStream_t s);
+                                int64_t Kp, const EpiArgs& e, int* err, void* sk_ws, size_t sk_bytes, int sk_mode,
+                                cudaStream_t s);
+// Stream-K tail decision for `tiles` pair tiles of nkb k-blocks on `pairs` resident pairs.
+bool tc_pair_stream_k(int64_t tiles, int64_t nkb, int64_t pairs, int mode);
+// Workspace of the tail for `pairs` resident pairs (partial slots and tile counters).
+size_t tc_pair_stream_k_bytes(int64_t pairs);
+// Workspace a pair-kernel plan reserves for the tail (0 when the tail would not run),
+// assuming sm_count / 2 resident pairs (152 SMs when sm_count is 0).
+size_t tc_pair_stream_k_workspace(int split, int64_t Mp, int64_t Np, int64_t Kp, int sm_count, int mode);
 
 }  // namespace mxg

@@ -20,6 +20,7 @@ struct Call {
   int split_k;         // 0 off, 1 automatic, >= 2 that many K slices (SIMT and DMMA methods)
   int sm_count;        // SMs of the device (0: assume 152) for the automatic split
   int cta_pairs;       // tensor-core methods: 0 automatic, 1 CTA pairs, 2 single CTAs
+  int stream_k;        // CTA-pair kernel's stream-K tail: 0 off, 1 automatic, 2 always
 };
 
 enum PlanKind : int { PLAN_NOOP = 0, PLAN_SCALE = 1, PLAN_GEMM = 2 };
@@ -47,6 +48,8 @@ struct Plan {
   int splits = 1;                   // split-K slices
   int64_t kslice = 0;               // k elements per slice
   size_t bytes_ws = 0;              // split-K partial sums
+  size_t bytes_sk = 0;              // stream-K tail of the CTA-pair kernel (after the rest)
+  int stream_k = 0;                 // its mode
   size_t bytes_a = 0, bytes_b = 0, workspace = 0;
 };
 

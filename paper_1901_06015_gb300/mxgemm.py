@@ -90,6 +90,8 @@ def lib():
             L.mxg_set_split_k.argtypes = [_vp, _i32]
             L.mxg_set_cta_pairs.restype = _i32
             L.mxg_set_cta_pairs.argtypes = [_vp, _i32]
+            L.mxg_set_stream_k.restype = _i32
+            L.mxg_set_stream_k.argtypes = [_vp, _i32]
             L.mxg_set_literal_alpha.restype = _i32
             L.mxg_set_literal_alpha.argtypes = [_vp, _i32]
             L.mxg_set_stream.restype = _i32
@@ -229,6 +231,13 @@ class Handle:
         st = lib().mxg_set_cta_pairs(self.h, int(mode))
         if st:
             raise MxgError(st, "mxg_set_cta_pairs")
+
+    def set_stream_k(self, mode):
+        """Stream-K tail of the CTA-pair kernel: 0 off, 1 automatic, 2 whenever the last
+        wave is partial (see mxg_set_stream_k)."""
+        st = lib().mxg_set_stream_k(self.h, int(mode))
+        if st:
+            raise MxgError(st, "mxg_set_stream_k")
 
     def set_literal_alpha(self, on):
         """Sec. 7.2's literal reading of a complex alpha for calls on this handle."""

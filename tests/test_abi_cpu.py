@@ -66,6 +66,27 @@ def test_every_combo_plans(combo):
     assert info.method in (1, 5)   # AUTO: FFMA for single, DFMA for double
 
 
+def test_stream_k_tail_workspace_follows_the_automatic_rule():
+    """The CTA-pair kernel's stream-K tail: the plan reserves its workspace (76 pairs of
+    a 152-SM device x 512 KB of FP32 partial slots, plus 76 x 8 tile counters rounded
+    to 256 bytes) exactly when the automatic rule would run it: a partial last wave at
+    most 4/5 full and at least 8 k-blocks of 64 binary16 elements per pair's range."""
+    sk = 76 * 512 * 1024 + 2560
+
+    def ws(m, n, k):
+        return mx.mxg_plan("hhhh", m, n, k, method="tc16").workspace_bytes
+
+    planes = lambda m, n, k: 2 * m * k + 2 * n * k      # one binary16 plane per operand
+    # 1024 pair tiles on 76 pairs: r = 36, 128 k-blocks per tile -> tail
+    assert ws(8192, 8192, 8192) == planes(8192, 8192, 8192) + sk
+    # 4096 tiles: r = 68 > 4/5 of 76 -> none
+    assert ws(16384, 16384, 1024) == planes(16384, 16384, 1024)
+    # r = 36 but 36 x 4 k-blocks < 8 per pair -> none
+    assert ws(8192, 8192, 256) == planes(8192, 8192, 256)
+    # 152 tiles fill two waves exactly -> none
+    assert ws(256 * 8, 256 * 19, 4096) == planes(2048, 4864, 4096)
+
+
 def test_whole_op_transpose_for_row_major_C():
     info = mx.mxg_plan("zzsd", 50, 40, 30, strides=((1, 50), (1, 30), (40, 1)))
     assert info.whole_op_transposed == 1
