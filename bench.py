@@ -534,6 +534,7 @@ def run_precision(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     h = mx.Handle(); h.set_stream(stream)
+    h.set_stream_k(args.stream_k)
     sizes = [int(x) for x in args.sizes.split(",")]
     methods = ["ffma", "tf32x3", "bf16x3"]
     results = []

@@ -214,12 +214,17 @@ def test_grouped_batching_configuration_sampled_blocks():
 
 
 def _solo16(p, meth):
-    """p run alone through mxgemm_ex with method meth; C as numpy (16-bit aware)."""
+    """p run alone through mxgemm_ex with method meth and whole tiles (the grouped
+    launch has no stream-K tail); C as numpy (16-bit aware)."""
     import paper_1901_06015_gb300 as mx
     from tests.gpu_util import from_device
     dA, dB, dC = to_device(p["A"]), to_device(p["B"]), to_device(p["C"])
-    mx.mxgemm_ex(None, meth, p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, comp=p["combo"][3])
+    h = mx.Handle()
+    h.set_stream(torch.cuda.current_stream())
+    h.set_stream_k(0)
+    mx.mxgemm_ex(h, meth, p["ta"], p["tb"], p["alpha"], dA, dB, p["beta"], dC, comp=p["combo"][3])
     torch.cuda.synchronize()
+    h.close()
     return from_device(dC, p["combo"][0])
 
 
