@@ -120,22 +120,21 @@ __device__ __forceinline__ EpiScalars<AccT, CDT> epi_scalars(const EpiArgs& e) {
   return {static_cast<AccT>(e.ar), static_cast<AccT>(e.ai), to_ct<CT>(e.br), to_ct<CT>(e.bi), e.ai == 0.0};
 }
 
-// Update C(i, j) with the product value (pr, pi), both in the computation precision
-// AccT, given C's old value from epi_load and the converted scalars. pi is ignored
+// The new value of a C element from the product value (pr, pi), both in the computation
+// precision AccT, C's old value from epi_load and the converted scalars. pi is ignored
 // unless MODE pairs two real results into one complex value. Order of operations
 // (Sec. 7.1): t = alpha*P rounded in AccT, cast to C's precision; beta*C formed in C's
 // precision; their sum rounded in C's precision.
 template <typename AccT, int CDT, int MODE>
-__device__ __forceinline__ void epi_update(const EpiArgs& e, const EpiScalars<AccT, CDT>& sc, int64_t i, int64_t j,
-                                           AccT pr, AccT pi, const COld<CDT>& old) {
+__device__ __forceinline__ COld<CDT> epi_value(const EpiArgs& e, const EpiScalars<AccT, CDT>& sc, AccT pr, AccT pi,
+                                               const COld<CDT>& old) {
   using CT = typename CStore<CDT>::T;
-  if (i >= e.m || j >= e.n) return;
-  CT* c = static_cast<CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
-  if (!MXG_DBG_OK(c_in_extent<CDT>(e, c), e.dbg)) return;
+  COld<CDT> r;
   if constexpr (!CStore<CDT>::cplx) {
     // C real: alpha and beta projected onto the real line (Sec. 7.2).
     const CT t = to_ct<CT>(mul_rn(sc.ar, pr));
-    c[0] = e.beta_zero ? t : add_rn(mul_rn(sc.br, old.re), t);
+    r.re = e.beta_zero ? t : add_rn(mul_rn(sc.br, old.re), t);
+    r.im = r.re;
   } else {
     AccT tr, ti;
     if constexpr (MODE == OUT_RE_ONLY) {
@@ -147,16 +146,30 @@ __device__ __forceinline__ void epi_update(const EpiArgs& e, const EpiScalars<Ac
     }
     const CT tcr = to_ct<CT>(tr), tci = to_ct<CT>(ti);
     if (e.beta_zero) {
-      c[0] = tcr;
-      c[1] = (MODE == OUT_RE_ONLY && sc.ai_zero) ? to_ct<CT>(0.0f) : tci;
+      r.re = tcr;
+      r.im = (MODE == OUT_RE_ONLY && sc.ai_zero) ? to_ct<CT>(0.0f) : tci;
     } else {
       const CT cr = old.re, ci = old.im;
       const CT bcr = sub_rn(mul_rn(sc.br, cr), mul_rn(sc.bi, ci));
       const CT bci = add_rn(mul_rn(sc.br, ci), mul_rn(sc.bi, cr));
-      c[0] = add_rn(bcr, tcr);
-      c[1] = (MODE == OUT_RE_ONLY && sc.ai_zero) ? bci : add_rn(bci, tci);
+      r.re = add_rn(bcr, tcr);
+      r.im = (MODE == OUT_RE_ONLY && sc.ai_zero) ? bci : add_rn(bci, tci);
     }
   }
+  return r;
+}
+
+// The same update, stored to C(i, j) when (i, j) lies inside C.
+template <typename AccT, int CDT, int MODE>
+__device__ __forceinline__ void epi_update(const EpiArgs& e, const EpiScalars<AccT, CDT>& sc, int64_t i, int64_t j,
+                                           AccT pr, AccT pi, const COld<CDT>& old) {
+  using CT = typename CStore<CDT>::T;
+  if (i >= e.m || j >= e.n) return;
+  CT* c = static_cast<CT*>(e.C) + (i * e.rs + j * e.cs) * (CStore<CDT>::cplx ? 2 : 1);
+  if (!MXG_DBG_OK(c_in_extent<CDT>(e, c), e.dbg)) return;
+  const COld<CDT> r = epi_value<AccT, CDT, MODE>(e, sc, pr, pi, old);
+  c[0] = r.re;
+  if constexpr (CStore<CDT>::cplx) c[1] = r.im;
 }
 
 // Load, update and store one element of C.

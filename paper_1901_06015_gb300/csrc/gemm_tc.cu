@@ -410,6 +410,26 @@ bool tc_make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int
 }
 cudaError_t tc_current_sm_count(int* out) { return current_sm_count(out); }
 
+bool tc_make_c_map(CUtensorMap* map, const void* C, int esz, int64_t rows, int64_t cols, int64_t ld_bytes,
+                   uint32_t box_rows, uint32_t box_cols) {
+  if (!get_encoder() || !C || rows <= 0 || cols <= 0) return false;
+  if ((reinterpret_cast<uintptr_t>(C) & 15u) || (ld_bytes & 15) || ld_bytes < rows * esz) return false;
+  if ((box_rows * static_cast<uint32_t>(esz)) % 16u || box_rows > 256 || box_cols > 256) return false;
+  const CUtensorMapDataType dtype = (esz == 2)   ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                    : (esz == 4) ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                    : (esz == 8) ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                                 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  if (esz != 2 && esz != 4 && esz != 8) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld_bytes)};
+  const cuuint32_t box[2] = {box_rows, box_cols};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = g_encode(map, dtype, 2, const_cast<void*>(C), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool tc_group_problem(TcGroupProb* p, int split, const void* const planes[4], int64_t Mp, int64_t Np, int64_t Kp,
                       const EpiArgs& e, int cdt, int mode) {
   if (!get_encoder()) return false;

@@ -278,5 +278,11 @@ bool tc_get_encoder();
 bool tc_make_map(CUtensorMap* map, const void* ptr, int split, int64_t rows, int64_t Kp, uint32_t rows_box,
                  uint32_t rowb);
 cudaError_t tc_current_sm_count(int* out);
+// 2-D map over C stored with unit row stride (rows x cols elements of esz = 2, 4 or 8
+// bytes, a complex element counted as one; column pitch ld_bytes), box (box_rows x
+// box_cols), no swizzle; elements past the edges read as zero. False when C, its pitch
+// or the box break a TMA alignment rule.
+bool tc_make_c_map(CUtensorMap* map, const void* C, int esz, int64_t rows, int64_t cols, int64_t ld_bytes,
+                   uint32_t box_rows, uint32_t box_cols);
 
 }  // namespace mxg
