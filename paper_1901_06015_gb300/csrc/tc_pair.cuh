@@ -355,60 +355,6 @@ __device__ __forceinline__ void pf_read(const uint8_t* chunk, int rl, int lane,
   }
 }
 
-// tc_epi_finish for C with unit row stride when the whole warp's chunk lies inside C:
-// one address computation per chunk and no per-element bounds test, so the 32
-// elements' updates form straight-line code (a test and branch per element left the
-// epilogue warps stalled on branch resolution). The values are those of epi_update.
-template <int CDT, int MODE>
-__device__ __forceinline__ void tc_epi_finish_pf(const EpiArgs& e, const EpiScalars<float, CDT>& sc, int64_t row,
-                                                 int64_t col0, const uint32_t (&v)[32], int lane,
-                                                 const COld<CDT> (&old)[TcChunk<MODE>::nold]) {
-  using CT = typename CStore<CDT>::T;
-  constexpr int W = CStore<CDT>::cplx ? 2 : 1;
-  bool in;
-  if constexpr (MODE == OUT_ROWPAIR) in = (row >> 1) < e.m && col0 + 32 <= e.n;
-  else if constexpr (MODE == OUT_COLPAIR) in = row < e.m && (col0 >> 1) + 16 <= e.n;
-  else in = row < e.m && col0 + 32 <= e.n;
-#ifdef MXG_DEBUG_BOUNDS
-  in = false;   // the debug build checks every address
-#endif
-  if (!__all_sync(0xffffffffu, in)) {
-    tc_epi_finish<CDT, MODE>(e, sc, row, col0, v, lane, old);
-    return;
-  }
-  const int64_t step = e.cs * W;   // elements of CT between neighbouring columns of C
-  if constexpr (MODE == OUT_ROWPAIR) {
-    const bool odd = (lane & 1) != 0;
-    CT* p = static_cast<CT*>(e.C) + ((row >> 1) + (col0 + (odd ? 1 : 0)) * e.cs) * W;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const float ve = __uint_as_float(v[2 * t]), vo = __uint_as_float(v[2 * t + 1]);
-      const float got = __shfl_xor_sync(0xffffffffu, odd ? ve : vo, 1);
-      const float pr = odd ? got : ve, pi = odd ? vo : got;
-      const COld<CDT> r = epi_value<float, CDT, MODE>(e, sc, pr, pi, old[t]);
-      p[2 * t * step] = r.re;
-      p[2 * t * step + 1] = r.im;
-    }
-  } else if constexpr (MODE == OUT_COLPAIR) {
-    CT* p = static_cast<CT*>(e.C) + (row + (col0 >> 1) * e.cs) * W;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const COld<CDT> r =
-          epi_value<float, CDT, MODE>(e, sc, __uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]), old[t]);
-      p[t * step] = r.re;
-      p[t * step + 1] = r.im;
-    }
-  } else {
-    CT* p = static_cast<CT*>(e.C) + (row + col0 * e.cs) * W;
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-      const COld<CDT> r = epi_value<float, CDT, MODE>(e, sc, __uint_as_float(v[jj]), 0.0f, old[jj]);
-      p[jj * step] = r.re;
-      if constexpr (W == 2) p[jj * step + 1] = r.im;
-    }
-  }
-}
-
 // The epilogue of one thread's row (as tc_epi_row) with the old C values taken from the
 // prefetch ring. False when a wait ran out or the pair aborted (stores of the remaining
 // chunks skipped).
@@ -427,7 +373,7 @@ __device__ __forceinline__ bool tc_epi_row_pf(const EpiArgs& e, const EpiScalars
     cring_release(cr, b, lane);
     uint32_t v[32];
     tmem_ld32(tbase + static_cast<uint32_t>(c0), v);
-    tc_epi_finish_pf<CDT, MODE>(e, sc, row, n0 + c0, v, lane, old);
+    tc_epi_finish<CDT, MODE>(e, sc, row, n0 + c0, v, lane, old);
   }
   return true;
 }
