@@ -224,9 +224,10 @@ int mxg_set_cta_pairs(mxg_handle h, int mode);
  * tile's partials in increasing k and applies the epilogue (Sec. 7.1) to the sum, so
  * the result is the same from run to run. It differs from a whole-tile run only in the
  * FP32 summation order along k; the stated bound holds for both. Automatic mode runs
- * the tail when the last wave is at most 4/5 full and each range has at least 8 k
- * blocks. The tail adds (SMs / 2) x 512 KB (+ counters) to the workspace; a caller
- * workspace that holds the rest of the plan but not this runs without the tail.
+ * the tail when the pairs left idle by the last wave are at least 6% of the whole run
+ * and each range has at least 16 k blocks. The tail adds (SMs / 2) x 512 KB (+
+ * counters) to the workspace; a caller workspace that holds the rest of the plan but
+ * not this runs without the tail.
  * mxgemm_noalloc and the server never use it. */
 int mxg_set_stream_k(mxg_handle h, int mode);
 

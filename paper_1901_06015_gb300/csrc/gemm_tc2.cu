@@ -23,8 +23,11 @@ bool tc_pair_stream_k(int64_t tiles, int64_t nkb, int64_t pairs, int mode) {
   // consecutive pairs c_first .. c_last, each taking one ticket)
   if (r == 0 || r * nkb < pairs) return false;
   if (mode >= 2) return true;
-  // automatic: the last wave at most 4/5 full, and at least 8 k-blocks per range
-  return 5 * r <= 4 * pairs && r * nkb >= 8 * pairs;
+  // automatic: the pairs idle in the last wave are at least 6% of the whole run, and
+  // every range holds at least 16 k-blocks (measured on GB300: with 13.5 waves of
+  // short tiles the partial sums cost more than the idle share they recover)
+  const int64_t full = tiles / pairs;
+  return 100 * (pairs - r) >= 6 * pairs * (full + 1) && r * nkb >= 16 * pairs;
 }
 
 size_t tc_pair_stream_k_bytes(int64_t pairs) {

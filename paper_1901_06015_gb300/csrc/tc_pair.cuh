@@ -691,30 +691,6 @@ cudaError_t launch_pair(const CUtensorMap* maps, PairArgs g, int sms, void* sk_w
   using F = PairFmt<SPLIT, RB>;
   const int64_t npairs = ((g.Mp + 2 * P_BM - 1) / (2 * P_BM)) * (g.Np / P_BN);
   const int64_t nkb = g.Kp * F::elem / RB;
-  // C prefetch: with a short k the epilogue bounds the kernel, so two operand stages
-  // suffice and the rest of the span holds C chunks (as many as 24); with a long k the
-  // ring keeps its stages (giving up at most two) and the rest holds two chunks or more
-  CUtensorMap cmap;
-  std::memset(&cmap, 0, sizeof(cmap));
-  g.stages = F::stages;
-  g.cpf = 0; g.ncb = 0; g.c_rows = 0; g.c_bytes = 0; g.c_rep = 1;
-  const int cesz = c_elem_bytes(g.cdt);
-  const int rep = (cesz > 8) ? cesz / 8 : 1;   // a double complex element is two 8-byte map elements
-  if (c_prefetch_enabled() && cesz > 0 && g.e.C && !g.e.beta_zero && g.e.rs == 1 && g.e.m > 0 && g.e.n > 0) {
-    const int rows = (g.mode == OUT_ROWPAIR) ? P_BM / 2 : P_BM;
-    const int cols = (g.mode == OUT_COLPAIR) ? 16 : 32;
-    const uint32_t cb = static_cast<uint32_t>(rows * cols * cesz);
-    // a long k keeps the ring, giving up at most two stages to hold two chunks
-    int stages = (nkb >= 8) ? F::stages : 2;
-    const int floor_st = (nkb >= 8) ? std::max(2, F::stages - 2) : 2;
-    while (stages > floor_st && P_SPAN - static_cast<uint32_t>(stages) * F::stage_bytes < 2 * cb) --stages;
-    const uint32_t room = P_SPAN - static_cast<uint32_t>(stages) * F::stage_bytes;
-    const int ncb = static_cast<int>(std::min<uint32_t>(P_NCB, room / cb));
-    if (ncb >= 2 && tc_make_c_map(&cmap, g.e.C, cesz / rep, g.e.m * rep, g.e.n, g.e.cs * cesz,
-                                  static_cast<uint32_t>(rows * rep), static_cast<uint32_t>(cols))) {
-      g.stages = stages; g.cpf = 1; g.ncb = ncb; g.c_rows = rows; g.c_bytes = cb; g.c_rep = rep;
-    }
-  }
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -744,6 +720,37 @@ cudaError_t launch_pair(const CUtensorMap* maps, PairArgs g, int sms, void* sk_w
     g.sk_cnt = reinterpret_cast<int*>(static_cast<char*>(sk_ws) + sk_part_bytes(resident));
     e = cudaMemsetAsync(g.sk_cnt, 0, static_cast<size_t>(g.sk_r) * 8 * sizeof(int), s);
     if (e != cudaSuccess) return e;
+  }
+  // C prefetch: with a short k the epilogue bounds the kernel, so two operand stages
+  // suffice and the rest of the span holds C chunks (as many as 24); with a long k the
+  // ring keeps its stages (giving up at most two) and the rest holds two chunks or more
+  CUtensorMap cmap;
+  std::memset(&cmap, 0, sizeof(cmap));
+  g.stages = F::stages;
+  g.cpf = 0; g.ncb = 0; g.c_rows = 0; g.c_bytes = 0; g.c_rep = 1;
+  const int cesz = c_elem_bytes(g.cdt);
+  const int rep = (cesz > 8) ? cesz / 8 : 1;   // a double complex element is two 8-byte map elements
+  // the loader pays off where the epilogue is exposed (up to 64 MMA steps per tile) or
+  // where the kernel variant that has it runs anyway (stream-K tail); with long tiles
+  // and no tail the whole-tile variant is faster (measured: 3% at 8192^3, TC16)
+  const int64_t mma_steps = nkb * (F::planes == 2 ? 3 : 1);
+  if (c_prefetch_enabled() && cesz > 0 && g.e.C && !g.e.beta_zero && g.e.rs == 1 && g.e.m > 0 && g.e.n > 0 &&
+      (g.sk_r > 0 || mma_steps <= 64)) {
+    const int rows = (g.mode == OUT_ROWPAIR) ? P_BM / 2 : P_BM;
+    const int cols = (g.mode == OUT_COLPAIR) ? 16 : 32;
+    const uint32_t cb = static_cast<uint32_t>(rows * cols * cesz);
+    // a long k keeps the ring: the one-pass ring (6 stages) gives up at most two stages
+    // to hold two chunks, the split forms' 3 stages none (measured: a double C on
+    // TF32x3 at 4096^3 ran 14% slower with two stages)
+    int stages = (nkb >= 8) ? F::stages : 2;
+    const int floor_st = (nkb >= 8) ? (F::stages >= 6 ? F::stages - 2 : F::stages) : 2;
+    while (stages > floor_st && P_SPAN - static_cast<uint32_t>(stages) * F::stage_bytes < 2 * cb) --stages;
+    const uint32_t room = P_SPAN - static_cast<uint32_t>(stages) * F::stage_bytes;
+    const int ncb = static_cast<int>(std::min<uint32_t>(P_NCB, room / cb));
+    if (ncb >= 2 && tc_make_c_map(&cmap, g.e.C, cesz / rep, g.e.m * rep, g.e.n, g.e.cs * cesz,
+                                  static_cast<uint32_t>(rows * rep), static_cast<uint32_t>(cols))) {
+      g.stages = stages; g.cpf = 1; g.ncb = ncb; g.c_rows = rows; g.c_bytes = cb; g.c_rep = rep;
+    }
   }
   if (ncl <= 0) return cudaErrorInvalidValue;
   cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl), 1, 1);

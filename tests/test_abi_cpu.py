@@ -69,22 +69,27 @@ def test_every_combo_plans(combo):
 def test_stream_k_tail_workspace_follows_the_automatic_rule():
     """The CTA-pair kernel's stream-K tail: the plan reserves its workspace (76 pairs of
     a 152-SM device x 512 KB of FP32 partial slots, plus 76 x 8 tile counters rounded
-    to 256 bytes) exactly when the automatic rule would run it: a partial last wave at
-    most 4/5 full and at least 8 k-blocks of 64 binary16 elements per pair's range."""
+    to 256 bytes) exactly when the automatic rule would run it: the pairs idle in the
+    partial last wave are at least 6% of the run, and each pair's range holds at least
+    16 k-blocks (64 elements of a 16-bit format each)."""
     sk = 76 * 512 * 1024 + 2560
 
-    def ws(m, n, k):
-        return mx.mxg_plan("hhhh", m, n, k, method="tc16").workspace_bytes
+    def ws(combo, m, n, k, method):
+        return mx.mxg_plan(combo, m, n, k, method=method).workspace_bytes
 
-    planes = lambda m, n, k: 2 * m * k + 2 * n * k      # one binary16 plane per operand
-    # 1024 pair tiles on 76 pairs: r = 36, 128 k-blocks per tile -> tail
-    assert ws(8192, 8192, 8192) == planes(8192, 8192, 8192) + sk
-    # 4096 tiles: r = 68 > 4/5 of 76 -> none
-    assert ws(16384, 16384, 1024) == planes(16384, 16384, 1024)
-    # r = 36 but 36 x 4 k-blocks < 8 per pair -> none
-    assert ws(8192, 8192, 256) == planes(8192, 8192, 256)
+    def planes(m, n, k, count):                       # 2-byte planes: count per operand
+        return count * 2 * (m * k + n * k)
+
+    # BF16x3 4096^3: 256 pair tiles, last wave 28 of 76 (48 idle over 4 waves: 16%) -> tail
+    assert ws("ssss", 4096, 4096, 4096, "bf16x3") == planes(4096, 4096, 4096, 2) + sk
+    # TC16 2048^3: 64 tiles, one partial wave (16% idle), 64 x 32 k-blocks -> tail
+    assert ws("hhhh", 2048, 2048, 2048, "tc16") == planes(2048, 2048, 2048, 1) + sk
+    # TC16 8192^3: 40 idle pairs over 14 waves (4%) -> none
+    assert ws("hhhh", 8192, 8192, 8192, "tc16") == planes(8192, 8192, 8192, 1)
+    # 2048 x 2048 x 512: 64 x 8 k-blocks, fewer than 16 per pair -> none
+    assert ws("hhhh", 2048, 2048, 512, "tc16") == planes(2048, 2048, 512, 1)
     # 152 tiles fill two waves exactly -> none
-    assert ws(256 * 8, 256 * 19, 4096) == planes(2048, 4864, 4096)
+    assert ws("hhhh", 256 * 8, 256 * 19, 4096, "tc16") == planes(2048, 4864, 4096, 1)
 
 
 def test_whole_op_transpose_for_row_major_C():
