@@ -172,3 +172,38 @@ def test_stream_k_tail_after_whole_tiles():
         got = from_device(outs[0][r0:r0 + 64, c0:c0 + 64], combo[0])
         err, _ = normwise_error(combo, got, ref, Ab, Bb, Cb, 1.0, 1.0)
         assert err <= tolerance(combo, k, method), (r0, c0, err)
+
+
+PF_CASES = [
+    # combo, (m, n, k), method: C types s, c (row and column pairs), z (16-byte elements), d
+    ("shhh", (300, 520, 96), "tc16"),
+    ("ckkh", (140, 270, 96), "tc16"),
+    ("zkkh", (150, 260, 64), "tc16"),
+    ("zbbb", (90, 130, 200), "tc16"),        # case 1c: Re(C) only
+    ("dhhh", (260, 300, 128), "tc16"),
+    ("cscs", (150, 260, 330), "bf16x3"),
+    ("ssss", (300, 600, 320), "bf16x3"),
+]
+
+
+@pytest.mark.parametrize("combo,shape,method", PF_CASES)
+def test_c_prefetch_equals_direct_loads(combo, shape, method):
+    """The pair kernel takes old C from its TMA prefetch ring when C has unit row stride
+    and reads it straight from global memory otherwise. The same C stored both ways
+    (column-major, and every other row of a larger buffer) gives the same result bit for
+    bit, ragged edges and every output mode included, within the bound of the oracle."""
+    from tests.gpu_util import run
+    m, n, k = shape
+    A, B, C0 = synth.problem(47, combo, m, n, k)
+    alpha = (1.25 - 0.5j) if all(synth.is_complex(t) for t in combo[:3]) else 1.5
+    beta = (-0.5 + 0.25j) if synth.is_complex(combo[0]) else -0.5
+    big = np.zeros((2 * m + 1, n), dtype=C0.dtype, order="F")
+    Cg = big[::2, :][:m, :]
+    Cg[...] = C0
+    assert Cg.strides[0] != Cg.itemsize           # no unit row stride: direct loads
+    got_col = run(combo, A, B, np.asfortranarray(C0), alpha, beta, method=method)
+    got_gen = run(combo, A, B, Cg, alpha, beta, method=method)
+    assert np.array_equal(synth.to_c128(got_col), synth.to_c128(got_gen)), combo
+    ref = oracle_mxgemm("n", "n", alpha, A, B, beta, C0.copy(), comp=combo[3])
+    err, _ = normwise_error(combo, got_col, ref, A, B, C0, alpha, beta)
+    assert err <= tolerance(combo, k, method, beta), (combo, method, err)
