@@ -12,7 +12,11 @@
 // 256 rows in the one-CTA kernel: a third fewer bytes from L2 per flop, in half as many
 // row requests (128-byte rows), which is what bounds the one-pass 16-bit form there.
 //
-// Roles (224 threads per CTA, one CTA per SM, persistent over pair tiles):
+// Two variants of the kernel: whole tiles with the epilogue warps loading old C (warps
+// 0..5, 192 threads), and the one with the stream-K tail and the C loader (warps 0..6,
+// 224 threads); the host picks per call (the loader where a tile has at most 64 MMA
+// steps or the tail runs, the tail when the last wave leaves enough pairs idle).
+// Roles (one CTA per SM, persistent over pair tiles):
 //   warp 0      TMA producer in both CTAs: its halves of A and B, in 128-byte k rows
 //               with the 128-byte swizzle, into its own 6- (split forms: 3-) stage
 //               ring (2 stages with a short k, see warp 6); the completion of both CTAs'
